@@ -1,0 +1,262 @@
+/*
+ * apf.h -- adaptive polynomial filtering for Hermitian interior eigenproblems
+ * on one NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * The library computes every eigenpair (lambda, v) of a sparse Hermitian
+ * matrix A with lambda in a given interval [a, b] (Sec. 1, Eq. (ori_problem)
+ * of Xu, Ni, Li and Zhang, "Adaptive Polynomial Filtering for Hermitian
+ * Interior Eigenproblems").  It runs filtered subspace iteration with the
+ * adaptive, damped Chebyshev expansion of the step function as the filter
+ * (Alg. 4, "AdaPolySI"): each outer step applies the filter by Clenshaw's
+ * recurrence (Alg. 2), orthonormalises with Cholesky QR, performs
+ * Rayleigh-Ritz, tests residuals, rejects spurious Ritz values (Eq. (tau_s))
+ * and locks converged pairs.  Every step runs in this library's CUDA kernels.
+ *
+ * Conventions
+ *  - Every function returns an apf_status; APF_OK (0) means success.
+ *    apf_status_string() names a status.  On error, output arguments are
+ *    left unchanged unless stated otherwise.
+ *  - Dense blocks are row-major: element (i, c) of an n x p block with
+ *    leading dimension ld sits at offset i*ld + c.  Complex values are
+ *    interleaved (re, im) pairs of the real type.
+ *  - "device" pointers are CUDA global-memory pointers on the context's
+ *    device; "host" pointers are ordinary CPU memory.  The library never
+ *    keeps a caller pointer beyond the call that received it.
+ *  - All device work is ordered on the context's stream; calls that return
+ *    host data synchronise that stream.
+ *  - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef APF_H
+#define APF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  APF_OK = 0,
+  APF_ERR_ARG = 1,             /* invalid argument (sizes, a > b, interval outside spectrum, ...) */
+  APF_ERR_OOM = 2,             /* device allocation failed */
+  APF_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+  APF_ERR_NOT_HERMITIAN = 4,   /* ingest found A != A^H beyond tolerance */
+  APF_ERR_CHOL = 5,            /* Cholesky QR broke down even with the shifted retry */
+  APF_ERR_NO_CONVERGENCE = 6,  /* max_iter reached; the result holds the pairs locked so far */
+  APF_ERR_EIGH = 7,            /* the small dense eigensolver did not converge */
+  APF_ERR_TIMEOUT = 8,         /* a device-side wait exceeded its time limit */
+  APF_ERR_NOT_READY = 9        /* the object has no data of the requested kind */
+} apf_status;
+
+typedef enum {
+  APF_R64 = 0,    /* real double */
+  APF_C128 = 1    /* complex double (re, im) */
+} apf_dtype;
+
+typedef enum {
+  APF_DAMP_LANCZOS_M = 0,  /* exponent-m Lanczos factors, Eq. (m_Lanczos_damping) (paper default) */
+  APF_DAMP_JACKSON = 1,    /* Jackson factors, Sec. 2.2 */
+  APF_DAMP_NONE = 2        /* no damping */
+} apf_damping;
+
+typedef enum {
+  /* Filter recurrence in FP64 (complex FP64 for Hermitian A). */
+  APF_FILTER_F64 = 0,
+  /* Filter recurrence in FP32 with FP32 accumulation.  Accurate to about
+   * 1e-7 relative: the residual stalls there (kept for comparison). */
+  APF_FILTER_F32 = 1,
+  /* FP32 recurrence on the defect: rho(A)V = V rho(Lambda) + D, where D
+   * obeys the Clenshaw recurrence driven by the Ritz residual
+   * R = A V - V Lambda.  The FP64 part is exact; the FP32 error scales with
+   * ||R||, so the iteration converges to FP64 accuracy.  First outer step
+   * (no Ritz values yet) uses APF_FILTER_F32. */
+  APF_FILTER_F32_DEFECT = 2
+} apf_filter_precision;
+
+typedef struct apf_ctx apf_ctx;
+typedef struct apf_matrix apf_matrix;
+typedef struct apf_result apf_result;
+
+/* Solver parameters.  apf_params_default() fills the paper's defaults
+ * (Sec. 4): m = 0.5, tau_a = 1e-3, C = 1.4, k = ceil(2.5 k^(1)), tau_c = 1e-10. */
+typedef struct {
+  double a, b;              /* interval of interest, a < b */
+  int64_t p;                /* subspace size (> 0, <= APF_MAX_P, <= n) */
+  int32_t k_fixed;          /* 0: adaptive degree (Eq. (compute_k_1), Alg. 3); > 0: fixed degree */
+  int32_t damping;          /* apf_damping */
+  double C;                 /* Eq. (compute_k_1) constant, 1.4 */
+  double k_ratio;           /* maximum degree k = ceil(k_ratio * k^(1)), 2.5 */
+  double m_d;               /* damping exponent m of Eq. (m_Lanczos_damping), 0.5 */
+  double tau_a;             /* adaptive threshold of Alg. 3, 1e-3 */
+  double tau_c;             /* convergence threshold: lock when ||r|| <= tau_c ||A||, 1e-10 */
+  int32_t max_iter;         /* outer iteration cap, 50 */
+  int32_t lanczos_steps;    /* Lanczos steps for the spectrum bounds (Sec. 3.4), 40 */
+  double bound_pad;         /* outward padding of the bounds, fraction of the Ritz spread, 0.01 */
+  int32_t filter_precision; /* apf_filter_precision, APF_FILTER_F64 */
+  int32_t spurious_rule;    /* 1: Alg. 4 lines 14-18 on (default); 0: off */
+  uint64_t seed;            /* seed of the initial block and Lanczos start vector */
+  const void* init_block;   /* optional n x p initial block (row-major, ld = p); NULL: seeded */
+  int32_t init_on_device;   /* 1 if init_block is a device pointer */
+  int32_t max_degree_cap;   /* safety cap on the maximum degree k, 100000 */
+} apf_params;
+
+/* Statistics of one solve (the metrics of Table 2 plus per-stage times). */
+typedef struct {
+  int32_t iterations;        /* outer iterations run */
+  int32_t k1, k_max;         /* initial degree k^(1) and maximum degree k */
+  double avg_degree;         /* mean filter degree over the iterations */
+  int64_t spmv_columns;      /* sparse matrix times vector products (columns), Table 2 "SpMVs" */
+  int64_t filter_launches;   /* Clenshaw step kernels launched */
+  int64_t gpu_launches;      /* all kernels launched by this solve */
+  double lambda_min, lambda_max;  /* estimated spectrum bounds */
+  double norm_a;             /* max(|lambda_min|, |lambda_max|) */
+  double ms_total, ms_setup, ms_filter, ms_orth, ms_rr, ms_check;  /* stage wall times */
+  double filter_kernel_ms;   /* summed device time of the Clenshaw SpMM launches (CUDA events) */
+  double filter_bytes;       /* algorithmic bytes of those launches */
+  double max_residual;       /* max ||A v - lambda v|| / ||A|| over the returned pairs */
+} apf_stats;
+
+#define APF_MAX_P 1024
+
+/* ---- context --------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to order all work on, or NULL for a stream owned by the context. */
+apf_status apf_create(apf_ctx** out, int device, void* cuda_stream);
+apf_status apf_destroy(apf_ctx* ctx);
+const char* apf_status_string(int status);
+/* Text of the last error recorded on this context ("" if none). */
+const char* apf_last_error_message(const apf_ctx* ctx);
+/* Kernels launched on this context since creation (a counter). */
+int64_t apf_launch_count(const apf_ctx* ctx);
+
+/* ---- matrices ---------------------------------------------------------- */
+
+/* Copy a sparse Hermitian matrix, given in CSR with both triangles stored,
+ * into the library's device layout (Sec. 3.3.1: CSR storage of A).
+ * rowptr: n + 1 int64 offsets, monotone, rowptr[0] = 0, rowptr[n] = nnz.
+ * colidx: nnz int32 column indices in [0, n).  vals: nnz values of `dtype`.
+ * `on_device` = 1 if the three arrays are device pointers, 0 if host.
+ * Missing diagonal entries are stored as explicit zeros.  The matrix is
+ * checked for A = A^H (relative tolerance 1e-12): APF_ERR_NOT_HERMITIAN. */
+apf_status apf_matrix_create_csr(apf_ctx* ctx, int64_t n, int64_t nnz,
+                                 const int64_t* rowptr, const int32_t* colidx,
+                                 const void* vals, int32_t dtype, int32_t on_device,
+                                 apf_matrix** out);
+
+/* Same, from SELL-C-sigma (Kreutzer et al. 2014): rows permuted by `perm`
+ * (perm[r] = original row stored at sorted position r), grouped in chunks of C
+ * rows stored column-major; chunk c holds chunk_len[c] * C entries starting at
+ * chunk_ptr[c]; padding entries have value 0.  Host pointers only.  The
+ * matrix is converted to CSR on ingest (same device layout as above). */
+apf_status apf_matrix_create_sell(apf_ctx* ctx, int64_t n, int32_t C, int32_t sigma,
+                                  const int64_t* perm, const int64_t* chunk_ptr,
+                                  const int32_t* chunk_len, const int32_t* colidx,
+                                  const void* vals, int32_t dtype, apf_matrix** out);
+apf_status apf_matrix_destroy(apf_matrix* A);
+apf_status apf_matrix_info(const apf_matrix* A, int64_t* n, int64_t* nnz, int32_t* dtype);
+
+/* ---- solve -------------------------------------------------------------- */
+
+void apf_params_default(apf_params* p);
+
+/* Alg. 4: all eigenpairs of A in [a, b].  On APF_OK or APF_ERR_NO_CONVERGENCE
+ * *out receives a result (to be freed with apf_result_destroy) holding the
+ * locked pairs in ascending order of eigenvalue. */
+apf_status apf_solve(apf_ctx* ctx, const apf_matrix* A, const apf_params* params,
+                     apf_result** out);
+apf_status apf_result_count(const apf_result* r, int64_t* e);
+/* e eigenvalues, ascending, to host memory. */
+apf_status apf_result_eigvals(const apf_result* r, double* host_out);
+/* n x e eigenvectors, column-major with leading dimension ld >= n (column j
+ * belongs to eigenvalue j), of the matrix dtype; `out_on_device` selects
+ * where `out` lives. */
+apf_status apf_result_eigvecs(const apf_result* r, void* out, int64_t ld, int32_t out_on_device);
+/* e relative residuals ||A v - lambda v|| / ||A|| to host memory. */
+apf_status apf_result_residuals(const apf_result* r, double* host_out);
+apf_status apf_result_stats(const apf_result* r, apf_stats* out);
+/* Per-iteration history, up to `cap` records of 6 doubles each:
+ * (degree, active width, e, locked this iteration, n_lock before, max in-interval residual / ||A||).
+ * Returns the number of records in *count. */
+apf_status apf_result_history(const apf_result* r, double* host_out, int32_t cap, int32_t* count);
+apf_status apf_result_destroy(apf_result* r);
+
+/* ---- the steps of the path, callable one by one (device buffers) ---------- */
+
+/* Alg. 4 line 1 (Sec. 2.2, Eq. (c_j), Eq. (m_Lanczos_damping)): the
+ * coefficients a_j = c_j d_{j,k}, j = 0..k, for the mapped interval
+ * [am, bm] inside (-1, 1), to host memory (k + 1 doubles). */
+apf_status apf_filter_coefficients(double am, double bm, int32_t k, int32_t damping,
+                                   double m_d, double* host_out);
+
+/* Alg. 3: the degree for the next iteration from p Ritz values (host),
+ * in-interval count e and coefficients a_0..a_k (host). */
+apf_status apf_degree_select(const double* ritz, int32_t p, int32_t e, const double* coef,
+                             int32_t k, double l1, double l2, double tau_a, int32_t* degree);
+
+/* Sec. 3.4: spectrum bounds by `steps` Lanczos steps (full
+ * reorthogonalisation) from the seeded start vector, padded outward by
+ * |beta_m s_m| + pad (theta_max - theta_min) and clipped to the Gershgorin
+ * interval.  host_out[6] = {lmin, lmax, theta_min, theta_max, gersh_lo, gersh_hi}. */
+apf_status apf_spectrum_bounds(apf_ctx* ctx, const apf_matrix* A, int32_t steps,
+                               uint64_t seed, double pad, double* host_out);
+
+/* Alg. 2: Y = rho(l(A)) X with rho = sum_{j=0}^{degree} coef[j] T_j and
+ * l(x) = l1 x + l2.  X, Y: device n x p blocks of the matrix dtype (X and Y
+ * may not overlap).  coef: host, degree + 1 doubles.  precision:
+ * APF_FILTER_F64 or APF_FILTER_F32. */
+apf_status apf_filter_apply(apf_ctx* ctx, const apf_matrix* A, const double* coef,
+                            int32_t degree, double l1, double l2, int32_t precision,
+                            const void* X, int64_t ldx, int64_t p, void* Y, int64_t ldy);
+
+/* Alg. 2 in the defect form of APF_FILTER_F32_DEFECT: Y = rho(l(A)) V using
+ * the FP64 identity rho(l(A)) V = V diag(rho(l(lam))) + D and an FP32
+ * recurrence for D driven by R = A V - V diag(lam).  V, AV: device n x p
+ * blocks (ld), lam: device p doubles. */
+apf_status apf_filter_apply_defect(apf_ctx* ctx, const apf_matrix* A, const double* coef,
+                                   int32_t degree, double l1, double l2, const void* V,
+                                   const void* AV, const double* lam, int64_t ld, int64_t p,
+                                   void* Y, int64_t ldy);
+
+/* Y = A X (FP64 sparse times dense block), device blocks. */
+apf_status apf_spmm(apf_ctx* ctx, const apf_matrix* A, const void* X, int64_t ldx,
+                    int64_t p, void* Y, int64_t ldy);
+
+/* G = X^H Y: the tall-skinny Gram product of the Cholesky QR and
+ * Rayleigh-Ritz steps (Alg. 4 lines 5 and 7).  X: n x pa, Y: n x pb,
+ * G: pa x pb row-major (ldg >= pb), all device, of `dtype`. */
+apf_status apf_gram(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t pb,
+                    const void* X, int64_t ldx, const void* Y, int64_t ldy,
+                    void* G, int64_t ldg);
+
+/* Alg. 4 line 5: X (device n x p) is replaced by Q with X = Q R, by CholQR2
+ * (shifted CholQR3 when the first factorisation breaks down). */
+apf_status apf_cholqr2(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t p, void* X, int64_t ld);
+
+/* Hermitian eigendecomposition B = U diag(w) U^H of a small p x p device
+ * matrix (p <= APF_MAX_P): w ascending (device), U row-major (ldu).
+ * One-sided Jacobi on B + s I, s = 2 ||B||_inf. */
+apf_status apf_eigh_small(apf_ctx* ctx, int32_t dtype, int64_t p, const void* B, int64_t ldb,
+                          double* w, void* U, int64_t ldu);
+
+/* Alg. 1 Rayleigh-Ritz: Q (device n x p, orthonormal columns) ->
+ * Ritz values w (device, ascending) and Ritz vectors V = Q U (device n x p). */
+apf_status apf_rayleigh_ritz(apf_ctx* ctx, const apf_matrix* A, const void* Q, int64_t ld,
+                             int64_t p, double* w, void* V, int64_t ldv);
+
+/* ||A v_j - w_j v_j||_2 for the p columns of V (device) into host_out[p]. */
+apf_status apf_residual_norms(apf_ctx* ctx, const apf_matrix* A, const void* V, int64_t ld,
+                              int64_t p, const double* w, double* host_out);
+
+/* The seeded initial block: entry (i, c) uniform in [-1, 1) from counter-based
+ * SplitMix64 (Steele, Lea and Flood 2014) keyed by (seed, stream); real entry
+ * uses counter i*p + c, complex entry counters 2(i*p + c) and 2(i*p + c) + 1. */
+apf_status apf_random_block(apf_ctx* ctx, int32_t dtype, uint64_t seed, uint32_t stream,
+                            int64_t n, int64_t p, void* X, int64_t ld);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APF_H */

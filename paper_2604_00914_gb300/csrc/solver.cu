@@ -1,0 +1,724 @@
+// AdaPolySI on one GPU: set-up (Sec. 3.4 bounds, Sec. 2.2 coefficients,
+// Eq. (compute_k_1)), then per outer iteration (Alg. 4): filter by Clenshaw
+// (Alg. 2) in FP64 or FP32, orthogonalisation against the locked vectors and
+// CholQR2, Rayleigh-Ritz, residuals, the spurious test (Eq. (tau_s)), locking
+// and the next degree (Alg. 3).  The dense and sparse work runs in the
+// library's kernels; the host handles the p Ritz values and index sets of each
+// iteration (one device-to-host transfer of 2 p doubles per iteration).
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <numeric>
+
+#include "host_math.h"
+#include "solver.h"
+
+namespace apf {
+
+// ---- Sec. 3.4: spectrum bounds ----------------------------------------------------
+template <class T>
+static void spectrum_bounds_t(apf_ctx* ctx, const apf_matrix* A, int steps, uint64_t seed,
+                              double pad, double out[6]) {
+  const int64_t n = A->n;
+  const int m = (int)std::min<int64_t>(steps, n);
+  APF_REQUIRE(m >= 1, APF_ERR_ARG);
+  const T* vals = static_cast<const T*>(A->vals);
+  DBuf Q((size_t)n * (m + 1) * sizeof(T), ctx->stream, true);
+  DBuf w((size_t)n * sizeof(T), ctx->stream, true);
+  DBuf cf((size_t)(m + 1) * sizeof(T), ctx->stream, true);
+  DBuf ab((size_t)(2 * m + 2) * sizeof(double), ctx->stream, true);
+  T* q = Q.as<T>();
+  double* alpha = ab.as<double>();
+  double* beta = alpha + m + 1;
+  random_block<T>(ctx, seed, 2u, n, 1, q, 1);
+  norm2<T>(ctx, n, q, beta + m);
+  scale_vec_by_inv<T>(ctx, n, q, beta + m, q);
+  std::vector<double> ha, hb;
+  for (int j = 0; j < m; ++j) {
+    spmv<T>(ctx, n, A->rowptr, A->colidx, vals, q + (int64_t)j * n, w.as<T>());
+    lanczos_update<T>(ctx, n, j, q, w.as<T>(), alpha, beta);
+    for (int pass = 0; pass < 2; ++pass) {
+      dot_many<T>(ctx, n, j + 1, q, w.as<T>(), cf.as<T>());
+      axpy_many<T>(ctx, n, j + 1, q, cf.as<T>(), w.as<T>());
+    }
+    norm2<T>(ctx, n, w.as<T>(), beta + j);
+    double hab[2];
+    APF_CUDA(cudaMemcpyAsync(&hab[0], alpha + j, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    APF_CUDA(cudaMemcpyAsync(&hab[1], beta + j, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    APF_CUDA(cudaStreamSynchronize(ctx->stream));
+    ha.push_back(hab[0]);
+    hb.push_back(hab[1]);
+    double amax = 1.0;
+    for (double v : ha) amax = std::max(amax, fabs(v));
+    if (j == m - 1 || hab[1] <= 1e-14 * amax) break;
+    scale_vec_by_inv<T>(ctx, n, w.as<T>(), beta + j, q + (int64_t)(j + 1) * n);
+  }
+  const int mm = (int)ha.size();
+  // tridiagonal T_m, eigenvalues and last components of its eigenvectors
+  std::vector<double> Th((size_t)mm * mm, 0.0);
+  for (int i = 0; i < mm; ++i) {
+    Th[(size_t)i * mm + i] = ha[(size_t)i];
+    if (i + 1 < mm) Th[(size_t)i * mm + i + 1] = Th[(size_t)(i + 1) * mm + i] = hb[(size_t)i];
+  }
+  DBuf Td((size_t)mm * mm * sizeof(double), ctx->stream, false);
+  DBuf Ud((size_t)mm * mm * sizeof(double), ctx->stream, false);
+  DBuf wd((size_t)mm * sizeof(double), ctx->stream, false);
+  APF_CUDA(cudaMemcpyAsync(Td.p, Th.data(), Th.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  eigh_jacobi<double>(ctx, mm, Td.as<double>(), mm, wd.as<double>(), Ud.as<double>(), mm);
+  std::vector<double> hw((size_t)mm), hU((size_t)mm * mm);
+  APF_CUDA(cudaMemcpyAsync(hw.data(), wd.p, hw.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  APF_CUDA(cudaMemcpyAsync(hU.data(), Ud.p, hU.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  APF_CUDA(cudaStreamSynchronize(ctx->stream));
+  const int derr = fetch_device_error(ctx);
+  if (derr == DEV_EIGH_NOCONV) throw ApfError{APF_ERR_EIGH, "Lanczos tridiagonal eigensolver"};
+  if (derr == DEV_BARRIER_TIMEOUT) throw ApfError{APF_ERR_TIMEOUT, "eigensolver barrier"};
+  const double th_lo = hw[0], th_hi = hw[(size_t)mm - 1];
+  const double blast = hb[(size_t)mm - 1];
+  const double res_lo = fabs(blast * hU[(size_t)(mm - 1) * mm + 0]);
+  const double res_hi = fabs(blast * hU[(size_t)(mm - 1) * mm + (mm - 1)]);
+  const double spread = th_hi - th_lo;
+  double lmax = th_hi + res_hi + pad * spread;
+  double lmin = th_lo - res_lo - pad * spread;
+  lmax = std::min(lmax, A->gersh_hi);
+  lmin = std::max(lmin, A->gersh_lo);
+  out[0] = lmin;
+  out[1] = lmax;
+  out[2] = th_lo;
+  out[3] = th_hi;
+  out[4] = A->gersh_lo;
+  out[5] = A->gersh_hi;
+}
+
+void spectrum_bounds(apf_ctx* ctx, const apf_matrix* A, int steps, uint64_t seed, double pad,
+                     double out[6]) {
+  if (A->dtype == APF_C128) spectrum_bounds_t<double2>(ctx, A, steps, seed, pad, out);
+  else spectrum_bounds_t<double>(ctx, A, steps, seed, pad, out);
+}
+
+// ---- Alg. 2: the Clenshaw recurrence over device buffers -------------------------------
+// Counters of the SpMM launches of one filter application.
+struct FilterCount {
+  int64_t launches = 0;
+  double bytes = 0.0;
+};
+
+static double step_bytes(int64_t n, int64_t nnz, int64_t p, size_t sval, size_t sblk, bool vin,
+                         bool y) {
+  const double mat = (double)nnz * (double)(sval + 4) + 8.0 * (double)(n + 1);
+  const double streams = 2.0 + (vin ? 1.0 : 0.0) + (y ? 1.0 : 0.0);
+  return mat + streams * (double)n * (double)p * (double)sblk;
+}
+
+// Plain form: returns the buffer (B1 or B2) that holds rho(A_hat) Y.
+// a: host coefficients a_0..a_k.  ev0/ev1 bracket the SpMM launches.
+template <class S>
+static S* clenshaw_plain(apf_ctx* ctx, int64_t n, int64_t nnz, const int64_t* rowptr,
+                         const int32_t* colidx, const S* Ahat, const S* Y, int64_t ld, int64_t p,
+                         const double* a, int k, S* B1, S* B2, cudaEvent_t ev0, cudaEvent_t ev1,
+                         FilterCount* fc) {
+  using Real = typename ScalarTraits<S>::Real;
+  if (k == 0) {
+    scale_block<S>(ctx, n, p, a[0], Y, ld, B1, ld);
+    if (ev0) { APF_CUDA(cudaEventRecord(ev0, ctx->stream)); APF_CUDA(cudaEventRecord(ev1, ctx->stream)); }
+    return B1;
+  }
+  scale_block<S>(ctx, n, p, a[k], Y, ld, B1, ld);  // b_k = a_k Y
+  S* P1 = B1;
+  S* P2 = nullptr;
+  if (ev0) APF_CUDA(cudaEventRecord(ev0, ctx->stream));
+  for (int j = k - 1; j >= 0; --j) {
+    S* out = P2 ? P2 : (P1 == B1 ? B2 : B1);
+    const Real alpha = (j == 0) ? (Real)1 : (Real)2;
+    clenshaw_step<S, S>(ctx, n, rowptr, colidx, Ahat, P1, P2, Y, ld, p, nullptr, (Real)a[j], alpha, out);
+    fc->launches += 1;
+    fc->bytes += step_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr, true);
+    P2 = P1;
+    P1 = out;
+  }
+  if (ev0) APF_CUDA(cudaEventRecord(ev1, ctx->stream));
+  return P1;
+}
+
+// Defect form: returns the buffer holding D (nullptr when D = 0, i.e. k = 0).
+// F: device per-column coefficients, row j at F + j ld (see defect_coefficients).
+template <class S>
+static S* clenshaw_defect(apf_ctx* ctx, int64_t n, int64_t nnz, const int64_t* rowptr,
+                          const int32_t* colidx, const S* Ahat, const S* R, int64_t ld, int64_t p,
+                          const float* F, int k, S* B1, S* B2, cudaEvent_t ev0, cudaEvent_t ev1,
+                          FilterCount* fc) {
+  if (k == 0) {
+    if (ev0) { APF_CUDA(cudaEventRecord(ev0, ctx->stream)); APF_CUDA(cudaEventRecord(ev1, ctx->stream)); }
+    return nullptr;
+  }
+  if (k == 1) {
+    scale_columns<S>(ctx, n, p, F, R, ld, B1);  // D = beta_1 R_hat
+    if (ev0) { APF_CUDA(cudaEventRecord(ev0, ctx->stream)); APF_CUDA(cudaEventRecord(ev1, ctx->stream)); }
+    return B1;
+  }
+  scale_columns<S>(ctx, n, p, F + (int64_t)(k - 1) * ld, R, ld, B1);  // D_{k-1} = 2 a_k R_hat
+  S* P1 = B1;
+  S* P2 = nullptr;  // D_k = 0
+  if (ev0) APF_CUDA(cudaEventRecord(ev0, ctx->stream));
+  for (int j = k - 2; j >= 0; --j) {
+    S* out = P2 ? P2 : (P1 == B1 ? B2 : B1);
+    const float alpha = (j == 0) ? 1.0f : 2.0f;
+    clenshaw_step<S, S>(ctx, n, rowptr, colidx, Ahat, P1, P2, R, ld, p, F + (int64_t)j * ld, 0.0f,
+                        alpha, out);
+    fc->launches += 1;
+    fc->bytes += step_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr, true);
+    P2 = P1;
+    P1 = out;
+  }
+  if (ev0) APF_CUDA(cudaEventRecord(ev1, ctx->stream));
+  return P1;
+}
+
+// Filter state of one solve: scaled copies of A and the recurrence buffers.
+template <class T>
+struct FilterState {
+  using TL = typename LowOf<T>::type;
+  apf_ctx* ctx = nullptr;
+  const apf_matrix* A = nullptr;
+  int64_t n = 0, ld = 0;
+  double l1 = 0, l2 = 0;
+  DBuf Ahat64, Ahat32;     // l1 A + l2 I in FP64 / FP32
+  DBuf B1, B2, Y32;        // recurrence buffers
+  DBuf coef_dev;           // a_j on the device (defect form)
+  DBuf F, rho;             // defect coefficients
+  std::vector<double> a;   // host a_j
+  int precision = APF_FILTER_F64;
+  int kmax = 0;
+
+  void init(apf_ctx* c, const apf_matrix* M, int64_t width_ld, double L1, double L2,
+            const std::vector<double>& coef, int prec) {
+    ctx = c;
+    A = M;
+    n = M->n;
+    ld = width_ld;
+    l1 = L1;
+    l2 = L2;
+    a = coef;
+    precision = prec;
+    kmax = (int)coef.size() - 1;
+    const T* vals = static_cast<const T*>(A->vals);
+    if (prec == APF_FILTER_F64) {
+      Ahat64.alloc((size_t)A->nnz * sizeof(T), ctx->stream, false);
+      scale_shift_matrix<T, T>(ctx, n, A->rowptr, A->colidx, vals, l1, l2, Ahat64.as<T>());
+      B1.alloc((size_t)n * ld * sizeof(T), ctx->stream, true);
+      B2.alloc((size_t)n * ld * sizeof(T), ctx->stream, true);
+    } else {
+      Ahat32.alloc((size_t)A->nnz * sizeof(TL), ctx->stream, false);
+      scale_shift_matrix<T, TL>(ctx, n, A->rowptr, A->colidx, vals, l1, l2, Ahat32.as<TL>());
+      B1.alloc((size_t)n * ld * sizeof(TL), ctx->stream, true);
+      B2.alloc((size_t)n * ld * sizeof(TL), ctx->stream, true);
+      Y32.alloc((size_t)n * ld * sizeof(TL), ctx->stream, true);
+      coef_dev.alloc(coef.size() * sizeof(double), ctx->stream, false);
+      APF_CUDA(cudaMemcpyAsync(coef_dev.p, coef.data(), coef.size() * sizeof(double),
+                               cudaMemcpyHostToDevice, ctx->stream));
+      F.alloc((size_t)(kmax + 1) * ld * sizeof(float), ctx->stream, true);
+      rho.alloc((size_t)ld * sizeof(double), ctx->stream, true);
+    }
+  }
+
+  // X = rho(A_hat) V with degree k; V, X: n x p (ld).  For the defect form AV
+  // and lam (device) hold A V and the Ritz values of V; pass nullptr to use the
+  // plain FP32 recurrence instead.
+  void apply(int k, const T* V, const T* AV, const double* lam, int64_t p, T* X, cudaEvent_t ev0,
+             cudaEvent_t ev1, FilterCount* fc) {
+    APF_REQUIRE(k <= kmax, APF_ERR_ARG);
+    const int64_t nnz = A->nnz;
+    if (precision == APF_FILTER_F64) {
+      T* out = clenshaw_plain<T>(ctx, n, nnz, A->rowptr, A->colidx, Ahat64.as<T>(), V, ld, p,
+                                 a.data(), k, B1.as<T>(), B2.as<T>(), ev0, ev1, fc);
+      copy_block<T>(ctx, n, p, out, ld, X, ld);
+      return;
+    }
+    if (precision == APF_FILTER_F32_DEFECT && AV != nullptr && lam != nullptr) {
+      // R_hat = l1 (A V - V diag(lam)) in FP32; norms are not needed here
+      DBuf scratch((size_t)p * sizeof(double), ctx->stream, false);
+      residual_norms<T>(ctx, n, p, AV, V, ld, lam, scratch.as<double>(), Y32.as<TL>(), l1);
+      defect_coefficients(ctx, p, ld, k, coef_dev.as<double>(), lam, l1, l2, F.as<float>(), rho.as<double>());
+      TL* D = clenshaw_defect<TL>(ctx, n, nnz, A->rowptr, A->colidx, Ahat32.as<TL>(), Y32.as<TL>(),
+                                  ld, p, F.as<float>(), k, B1.as<TL>(), B2.as<TL>(), ev0, ev1, fc);
+      defect_combine<T>(ctx, n, p, V, ld, rho.as<double>(), D, ld, X, ld);
+      return;
+    }
+    cast_block<T, TL>(ctx, n, p, V, ld, Y32.as<TL>(), ld);
+    TL* out = clenshaw_plain<TL>(ctx, n, nnz, A->rowptr, A->colidx, Ahat32.as<TL>(), Y32.as<TL>(),
+                                 ld, p, a.data(), k, B1.as<TL>(), B2.as<TL>(), ev0, ev1, fc);
+    cast_block<TL, T>(ctx, n, p, out, ld, X, ld);
+  }
+};
+
+// ---- Alg. 4 line 5: Cholesky QR ------------------------------------------------------
+template <class T>
+static bool cholesky_checked(apf_ctx* ctx, int64_t p, T* G, int64_t ldg, double shift) {
+  cholesky_upper<T>(ctx, p, G, ldg, shift);
+  const int e = fetch_device_error(ctx);
+  if (e == DEV_CHOL_PIVOT) return false;
+  if (e != 0) throw ApfError{APF_ERR_CUDA, "device error in Cholesky"};
+  return true;
+}
+
+// Small p x p workspace of the orthogonalisation and Rayleigh-Ritz steps.
+template <class T>
+struct SmallWork {
+  DBuf buf;
+  int64_t p = 0;
+  T *G, *Ri, *G3, *T1, *B, *U, *M, *C;
+  double* w;
+  void init(int64_t pmax, cudaStream_t s) {
+    p = pmax;
+    const size_t mat = (size_t)pmax * pmax;
+    buf.alloc(mat * 8 * sizeof(T) + (size_t)pmax * sizeof(double) + 256, s, true);
+    T* b = buf.as<T>();
+    G = b;
+    Ri = b + mat;
+    G3 = b + 2 * mat;
+    T1 = b + 3 * mat;
+    B = b + 4 * mat;
+    U = b + 5 * mat;
+    M = b + 6 * mat;
+    C = b + 7 * mat;
+    w = reinterpret_cast<double*>(b + 8 * mat);
+  }
+};
+
+// One Cholesky QR pass Xout = X R^{-1}, R from G = X^H X (+ shift I).
+template <class T>
+static bool cholqr_pass(apf_ctx* ctx, int64_t n, int64_t p, const T* X, int64_t ld, T* Xout,
+                        SmallWork<T>& sw, bool shifted) {
+  gram<T>(ctx, n, p, p, X, ld, X, ld, sw.G, p, true);
+  double shift = 0.0;
+  if (shifted) {
+    // shifted Cholesky QR (Fukaya et al. 2020): s = 11 (n p + p (p + 1)) u ||X||_F^2
+    std::vector<T> hG((size_t)p * p);
+    APF_CUDA(cudaMemcpyAsync(hG.data(), sw.G, hG.size() * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+    APF_CUDA(cudaStreamSynchronize(ctx->stream));
+    double tr = 0.0;
+    for (int64_t i = 0; i < p; ++i) tr += real_(hG[(size_t)(i * p + i)]);
+    shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * 1.1102230246251565e-16 * tr;
+  }
+  if (!cholesky_checked<T>(ctx, p, sw.G, p, shift)) return false;
+  tri_inv_upper<T>(ctx, p, sw.G, p, sw.Ri, p);
+  gemm_tall<T>(ctx, n, p, p, X, ld, sw.Ri, p, Xout, ld, 1.0, 0.0, nullptr, ld, true);
+  return true;
+}
+
+// CholQR2 of X into X (X1 is scratch of the same shape).  Shifted CholQR3 when
+// the first factorisation breaks down.
+template <class T>
+static void cholqr2_inplace(apf_ctx* ctx, int64_t n, int64_t p, T* X, T* X1, int64_t ld,
+                            SmallWork<T>& sw) {
+  if (!cholqr_pass<T>(ctx, n, p, X, ld, X1, sw, false)) {
+    if (!cholqr_pass<T>(ctx, n, p, X, ld, X1, sw, true)) throw ApfError{APF_ERR_CHOL, "shifted CholQR"};
+    if (!cholqr_pass<T>(ctx, n, p, X1, ld, X, sw, false)) throw ApfError{APF_ERR_CHOL, "CholQR3"};
+    copy_block<T>(ctx, n, p, X, ld, X1, ld);
+  }
+  if (!cholqr_pass<T>(ctx, n, p, X1, ld, X, sw, false)) throw ApfError{APF_ERR_CHOL, "CholQR2"};
+}
+
+template <class T>
+static void spmm_plain(apf_ctx* ctx, const apf_matrix* A, const T* X, int64_t ld, int64_t p, T* Y) {
+  clenshaw_step<T, T>(ctx, A->n, A->rowptr, A->colidx, static_cast<const T*>(A->vals), X, nullptr,
+                      nullptr, ld, p, nullptr, 0.0, 1.0, Y);
+}
+
+// Alg. 4 lines 5-7 and 13: X (filtered, n x p, destroyed) ->
+// Vh = Ritz vectors, AVh = A Vh, w = Ritz values (ascending), res = residual norms.
+// CholQR2's second pass is merged with Rayleigh-Ritz:
+//   X1 = X R1^{-1};  G2 = X1^H X1 = R2^H R2;  G3 = X1^H (A X1);
+//   B = R2^{-H} G3 R2^{-1} = Q^H A Q for Q = X1 R2^{-1};  B = U diag(w) U^H;
+//   Vh = Q U = X1 (R2^{-1} U).
+template <class T>
+static void orth_rr(apf_ctx* ctx, const apf_matrix* A, int64_t p, int64_t ld, T* X, T* X1,
+                    const T* Vlock, int64_t nlock, int64_t ldl, SmallWork<T>& sw, T* Vh, T* AVh,
+                    double* w, double* res) {
+  const int64_t n = A->n;
+  for (int pass = 0; pass < 2 && nlock > 0; ++pass) {
+    gram<T>(ctx, n, nlock, p, Vlock, ldl, X, ld, sw.C, p, false);
+    gemm_tall<T>(ctx, n, nlock, p, Vlock, ldl, sw.C, p, X, ld, -1.0, 1.0, X, ld, false);
+  }
+  if (!cholqr_pass<T>(ctx, n, p, X, ld, X1, sw, false)) {
+    if (!cholqr_pass<T>(ctx, n, p, X, ld, X1, sw, true)) throw ApfError{APF_ERR_CHOL, "shifted CholQR"};
+    if (!cholqr_pass<T>(ctx, n, p, X1, ld, X, sw, false)) throw ApfError{APF_ERR_CHOL, "CholQR3"};
+    copy_block<T>(ctx, n, p, X, ld, X1, ld);
+  }
+  T* AX = X;  // X is dead: reuse it for A X1
+  spmm_plain<T>(ctx, A, X1, ld, p, AX);
+  gram<T>(ctx, n, p, p, X1, ld, X1, ld, sw.G, p, true);
+  gram<T>(ctx, n, p, p, X1, ld, AX, ld, sw.G3, p, false);
+  if (!cholesky_checked<T>(ctx, p, sw.G, p, 0.0)) throw ApfError{APF_ERR_CHOL, "CholQR2 second pass"};
+  tri_inv_upper<T>(ctx, p, sw.G, p, sw.Ri, p);
+  small_gemm<T>(ctx, p, p, p, 'N', sw.G3, p, 'N', sw.Ri, p, sw.T1, p, 1.0, 0.0);
+  small_gemm<T>(ctx, p, p, p, 'H', sw.Ri, p, 'N', sw.T1, p, sw.B, p, 1.0, 0.0);
+  symmetrize<T>(ctx, p, sw.B, p);
+  eigh_jacobi<T>(ctx, p, sw.B, p, w, sw.U, p);
+  small_gemm<T>(ctx, p, p, p, 'N', sw.Ri, p, 'N', sw.U, p, sw.M, p, 1.0, 0.0);
+  gemm_tall<T>(ctx, n, p, p, X1, ld, sw.M, p, Vh, ld, 1.0, 0.0, nullptr, ld, false);
+  spmm_plain<T>(ctx, A, Vh, ld, p, AVh);
+  residual_norms<T>(ctx, n, p, AVh, Vh, ld, w, res, nullptr, 0.0);
+}
+
+// ---- Alg. 4 ---------------------------------------------------------------------------
+static double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) { cudaGetLastError(); return 0.0; }
+  return (double)ms;
+}
+
+struct EventPool {
+  std::vector<cudaEvent_t> ev;
+  cudaEvent_t get() {
+    cudaEvent_t e;
+    APF_CUDA(cudaEventCreate(&e));
+    ev.push_back(e);
+    return e;
+  }
+  ~EventPool() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+template <class T>
+static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, apf_result* out) {
+  using clock = std::chrono::steady_clock;
+  const auto t_start = clock::now();
+  const int64_t n = A->n;
+  const int64_t p = prm->p;
+  APF_REQUIRE(p >= 1 && p <= n && p <= APF_MAX_P, APF_ERR_ARG);
+  APF_REQUIRE(prm->a < prm->b, APF_ERR_ARG);
+  APF_REQUIRE(prm->max_iter >= 1, APF_ERR_ARG);
+  APF_REQUIRE(prm->filter_precision >= APF_FILTER_F64 && prm->filter_precision <= APF_FILTER_F32_DEFECT,
+              APF_ERR_ARG);
+  const int64_t launches0 = ctx->launches;
+  apf_stats st{};
+
+  // set-up (Alg. 4 line 1): bounds, map, degrees, coefficients
+  double bnd[6];
+  spectrum_bounds(ctx, A, prm->lanczos_steps, prm->seed, prm->bound_pad, bnd);
+  const double lmin = bnd[0], lmax = bnd[1];
+  const double l1 = 2.0 / (lmax - lmin), l2 = -(lmax + lmin) / (lmax - lmin);
+  const double normA = std::max(fabs(lmin), fabs(lmax));
+  const double am = l1 * prm->a + l2, bm = l1 * prm->b + l2;
+  APF_REQUIRE(am > -1.0 && bm < 1.0 && am < bm, APF_ERR_ARG);
+  int k1, kmax;
+  if (prm->k_fixed > 0) {
+    k1 = kmax = prm->k_fixed;
+  } else {
+    k1 = initial_degree(am, bm, prm->C);
+    kmax = (int)ceil(prm->k_ratio * k1);
+  }
+  APF_REQUIRE(k1 >= 0 && kmax <= prm->max_degree_cap, APF_ERR_ARG);
+  const std::vector<double> coef = filter_coefficients(am, bm, kmax, prm->damping, prm->m_d);
+  st.k1 = k1;
+  st.k_max = kmax;
+  st.lambda_min = lmin;
+  st.lambda_max = lmax;
+  st.norm_a = normA;
+
+  const int64_t ld = block_ld(p);
+  const size_t blk = (size_t)n * ld * sizeof(T);
+  DBuf Vh(blk, ctx->stream, true), AVh(blk, ctx->stream, true), X(blk, ctx->stream, true),
+      X1(blk, ctx->stream, true), Vlock(blk, ctx->stream, true);
+  DBuf wv(sizeof(double) * (size_t)(2 * ld + 8), ctx->stream, true);
+  DBuf resv(sizeof(double) * (size_t)(ld + 8), ctx->stream, true);
+  DBuf idxd(sizeof(int32_t) * (size_t)(2 * ld + 8), ctx->stream, false);
+  double* w = wv.as<double>();
+  double* w2 = w + ld;
+  double* res = resv.as<double>();
+  SmallWork<T> sw;
+  sw.init(p, ctx->stream);
+  FilterState<T> fs;
+  fs.init(ctx, A, ld, l1, l2, coef, prm->filter_precision);
+
+  // Alg. 4 line 2: orthonormal initial block
+  if (prm->init_block) {
+    APF_CUDA(cudaMemcpy2DAsync(Vh.p, ld * sizeof(T), prm->init_block, p * sizeof(T), p * sizeof(T), n,
+                               prm->init_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               ctx->stream));
+  } else {
+    random_block<T>(ctx, prm->seed, 1u, n, p, Vh.as<T>(), ld);
+  }
+  cholqr2_inplace<T>(ctx, n, p, Vh.as<T>(), X1.as<T>(), ld, sw);
+  APF_CUDA(cudaStreamSynchronize(ctx->stream));
+  st.ms_setup = std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
+
+  EventPool evp;
+  struct IterEv { cudaEvent_t e0, e1, e2, e3, f0, f1; };
+  std::vector<IterEv> iev;
+  std::vector<double> lam_lock;
+  std::vector<double> hist;
+  int64_t pa = p, nlock = 0;
+  int ki = k1, n_check_prev = 0;
+  bool have_ritz = false;  // Vh holds Ritz vectors with values in w and A Vh in AVh
+  apf_status status = APF_ERR_NO_CONVERGENCE;
+  FilterCount fc;
+  std::vector<double> hw((size_t)p), hr((size_t)p);
+  double deg_sum = 0.0;
+  int iters = 0;
+  for (int it = 1; it <= prm->max_iter; ++it) {
+    IterEv ev{evp.get(), evp.get(), evp.get(), evp.get(), evp.get(), evp.get()};
+    iev.push_back(ev);
+    APF_CUDA(cudaEventRecord(ev.e0, ctx->stream));
+    // line 4: filtering (Alg. 2)
+    const bool defect = have_ritz && prm->filter_precision == APF_FILTER_F32_DEFECT;
+    fs.apply(ki, Vh.as<T>(), defect ? AVh.as<T>() : nullptr, defect ? w : nullptr, pa, X.as<T>(),
+             ev.f0, ev.f1, &fc);
+    st.spmv_columns += (int64_t)ki * pa + 2 * pa;
+    deg_sum += ki;
+    ++iters;
+    APF_CUDA(cudaEventRecord(ev.e1, ctx->stream));
+    // lines 5-7 and 13: orthogonalisation, Rayleigh-Ritz, residuals
+    orth_rr<T>(ctx, A, pa, ld, X.as<T>(), X1.as<T>(), Vlock.as<T>(), nlock, ld, sw, Vh.as<T>(),
+               AVh.as<T>(), w, res);
+    APF_CUDA(cudaEventRecord(ev.e2, ctx->stream));
+    APF_CUDA(cudaMemcpyAsync(hw.data(), w, (size_t)pa * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    APF_CUDA(cudaMemcpyAsync(hr.data(), res, (size_t)pa * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    const int derr = fetch_device_error(ctx);  // synchronises
+    if (derr == DEV_EIGH_NOCONV) throw ApfError{APF_ERR_EIGH, "Rayleigh-Ritz eigensolver"};
+    if (derr == DEV_BARRIER_TIMEOUT) throw ApfError{APF_ERR_TIMEOUT, "eigensolver barrier"};
+    if (derr != 0) throw ApfError{APF_ERR_CUDA, "device error"};
+    have_ritz = true;
+    // line 8: in-interval set
+    std::vector<int> I;
+    for (int c = 0; c < pa; ++c)
+      if (hw[(size_t)c] >= prm->a && hw[(size_t)c] <= prm->b) I.push_back(c);
+    const int e = (int)I.size();
+    double maxres = 0.0;
+    for (int c : I) maxres = std::max(maxres, hr[(size_t)c] / normA);
+    std::vector<double> rec = {(double)ki, (double)pa, (double)e, 0.0, (double)nlock, maxres};
+    if (e == 0) {  // lines 9-11
+      APF_CUDA(cudaEventRecord(ev.e3, ctx->stream));
+      hist.insert(hist.end(), rec.begin(), rec.end());
+      continue;
+    }
+    // line 12: next degree (Alg. 3)
+    const int k_next = prm->k_fixed > 0 ? ki
+                                        : degree_select(hw.data(), (int)pa, e, coef.data(), kmax, l1, l2, prm->tau_a);
+    // lines 14-18: spurious Ritz values
+    if (prm->spurious_rule) {
+      double tau_s = 1e300;
+      for (int c : I) tau_s = std::min(tau_s, std::min(fabs(hw[(size_t)c] - prm->a), fabs(hw[(size_t)c] - prm->b)));
+      std::vector<int> Cs;
+      for (int c : I)
+        if (hr[(size_t)c] < tau_s) Cs.push_back(c);
+      const int n_check = (int)Cs.size() + (int)nlock;
+      if (n_check > 0 && n_check == n_check_prev) I = Cs;
+      n_check_prev = n_check;
+    }
+    // lines 19-21: lock
+    std::vector<int> L, keep;
+    std::vector<char> inL((size_t)pa, 0);
+    for (int c : I)
+      if (hr[(size_t)c] <= prm->tau_c * normA) { L.push_back(c); inL[(size_t)c] = 1; }
+    for (int c = 0; c < pa; ++c)
+      if (!inL[(size_t)c]) keep.push_back(c);
+    rec[3] = (double)L.size();
+    hist.insert(hist.end(), rec.begin(), rec.end());
+    const bool done = L.size() == I.size();
+    if (!L.empty()) {
+      std::vector<int32_t> idx(L.begin(), L.end());
+      idx.insert(idx.end(), keep.begin(), keep.end());
+      APF_CUDA(cudaMemcpyAsync(idxd.p, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+      const int32_t* dL = idxd.as<int32_t>();
+      const int32_t* dK = dL + L.size();
+      gather_columns<T>(ctx, n, (int64_t)L.size(), dL, Vh.as<T>(), ld, Vlock.as<T>() + nlock, ld);
+      for (int c : L) lam_lock.push_back(hw[(size_t)c]);
+      nlock += (int64_t)L.size();
+      const int64_t nk = (int64_t)keep.size();
+      if (nk > 0) {
+        gather_columns<T>(ctx, n, nk, dK, Vh.as<T>(), ld, X.as<T>(), ld);
+        copy_block<T>(ctx, n, nk, X.as<T>(), ld, Vh.as<T>(), ld);
+        gather_columns<T>(ctx, n, nk, dK, AVh.as<T>(), ld, X.as<T>(), ld);
+        copy_block<T>(ctx, n, nk, X.as<T>(), ld, AVh.as<T>(), ld);
+        gather_doubles(ctx, nk, dK, w, w2);
+        APF_CUDA(cudaMemcpyAsync(w, w2, (size_t)nk * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+      pa = nk;
+      // the filter buffers' padding columns must stay zero: clear the tail
+      if (pa < ld) {
+        APF_CUDA(cudaMemset2DAsync(Vh.as<T>() + pa, ld * sizeof(T), 0, (size_t)(ld - pa) * sizeof(T), n, ctx->stream));
+        APF_CUDA(cudaMemset2DAsync(AVh.as<T>() + pa, ld * sizeof(T), 0, (size_t)(ld - pa) * sizeof(T), n, ctx->stream));
+      }
+    }
+    APF_CUDA(cudaEventRecord(ev.e3, ctx->stream));
+    ki = k_next;
+    if (done) {  // lines 22-24
+      status = APF_OK;
+      break;
+    }
+    if (pa == 0) break;
+  }
+  APF_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (auto& ev : iev) {
+    st.ms_filter += elapsed_ms(ev.e0, ev.e1);
+    st.ms_rr += elapsed_ms(ev.e1, ev.e2);
+    st.ms_check += elapsed_ms(ev.e2, ev.e3);
+    st.filter_kernel_ms += elapsed_ms(ev.f0, ev.f1);
+  }
+  st.iterations = iters;
+  st.avg_degree = iters ? deg_sum / iters : 0.0;
+  st.filter_launches = fc.launches;
+  st.filter_bytes = fc.bytes;
+
+  // sorted result and its residuals
+  const int64_t e = (int64_t)lam_lock.size();
+  std::vector<int32_t> order((size_t)e);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t u, int32_t v) { return lam_lock[(size_t)u] < lam_lock[(size_t)v]; });
+  out->ctx = ctx;
+  out->n = n;
+  out->e = e;
+  out->dtype = A->dtype;
+  out->lde = block_ld(e);
+  out->lam.resize((size_t)e);
+  out->res.assign((size_t)e, 0.0);
+  for (int64_t j = 0; j < e; ++j) out->lam[(size_t)j] = lam_lock[(size_t)order[(size_t)j]];
+  out->vecs.alloc((size_t)n * out->lde * sizeof(T), ctx->stream, true);
+  if (e > 0) {
+    DBuf od((size_t)e * sizeof(int32_t), ctx->stream, false);
+    DBuf lamd((size_t)e * sizeof(double), ctx->stream, false);
+    APF_CUDA(cudaMemcpyAsync(od.p, order.data(), (size_t)e * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    APF_CUDA(cudaMemcpyAsync(lamd.p, out->lam.data(), (size_t)e * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    gather_columns<T>(ctx, n, e, od.as<int32_t>(), Vlock.as<T>(), ld, out->vecs.as<T>(), out->lde);
+    DBuf AVr((size_t)n * out->lde * sizeof(T), ctx->stream, true);
+    spmm_plain<T>(ctx, A, out->vecs.as<T>(), out->lde, e, AVr.as<T>());
+    DBuf rd((size_t)e * sizeof(double), ctx->stream, false);
+    residual_norms<T>(ctx, n, e, AVr.as<T>(), out->vecs.as<T>(), out->lde, lamd.as<double>(), rd.as<double>(), nullptr, 0.0);
+    APF_CUDA(cudaMemcpyAsync(out->res.data(), rd.p, (size_t)e * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    APF_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (auto& r : out->res) r /= normA;
+  }
+  st.max_residual = 0.0;
+  for (double r : out->res) st.max_residual = std::max(st.max_residual, r);
+  st.gpu_launches = ctx->launches - launches0;
+  st.ms_total = std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
+  out->history = hist;
+  out->stats = st;
+  if (status != APF_OK) throw ApfError{status, "no convergence"};
+}
+
+void solve(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, apf_result* out) {
+  if (A->dtype == APF_C128) solve_t<double2>(ctx, A, prm, out);
+  else solve_t<double>(ctx, A, prm, out);
+}
+
+// ---- the steps one by one, on caller buffers ------------------------------------------
+template <class T>
+static DBuf stage_in(apf_ctx* ctx, int64_t n, int64_t p, const T* X, int64_t ldx, int64_t ld) {
+  DBuf b((size_t)n * ld * sizeof(T), ctx->stream, true);
+  APF_CUDA(cudaMemcpy2DAsync(b.p, ld * sizeof(T), X, ldx * sizeof(T), p * sizeof(T), n,
+                             cudaMemcpyDeviceToDevice, ctx->stream));
+  return b;
+}
+
+template <class T>
+static void stage_out(apf_ctx* ctx, int64_t n, int64_t p, const T* X, int64_t ld, T* Y, int64_t ldy) {
+  APF_CUDA(cudaMemcpy2DAsync(Y, ldy * sizeof(T), X, ld * sizeof(T), p * sizeof(T), n,
+                             cudaMemcpyDeviceToDevice, ctx->stream));
+  APF_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+template <class T>
+void filter_apply_public(apf_ctx* ctx, const apf_matrix* A, const double* coef, int k, double l1,
+                         double l2, int precision, const T* X, int64_t ldx, int64_t p, T* Y,
+                         int64_t ldy) {
+  const int64_t n = A->n, ld = block_ld(p);
+  DBuf V = stage_in<T>(ctx, n, p, X, ldx, ld);
+  DBuf out((size_t)n * ld * sizeof(T), ctx->stream, true);
+  FilterState<T> fs;
+  fs.init(ctx, A, ld, l1, l2, std::vector<double>(coef, coef + k + 1), precision);
+  FilterCount fc;
+  fs.apply(k, V.as<T>(), nullptr, nullptr, p, out.as<T>(), nullptr, nullptr, &fc);
+  stage_out<T>(ctx, n, p, out.as<T>(), ld, Y, ldy);
+}
+
+template <class T>
+void filter_apply_defect_public(apf_ctx* ctx, const apf_matrix* A, const double* coef, int k,
+                                double l1, double l2, const T* V, const T* AV, const double* lam,
+                                int64_t ld_in, int64_t p, T* Y, int64_t ldy) {
+  const int64_t n = A->n, ld = block_ld(p);
+  DBuf Vb = stage_in<T>(ctx, n, p, V, ld_in, ld);
+  DBuf AVb = stage_in<T>(ctx, n, p, AV, ld_in, ld);
+  DBuf out((size_t)n * ld * sizeof(T), ctx->stream, true);
+  FilterState<T> fs;
+  fs.init(ctx, A, ld, l1, l2, std::vector<double>(coef, coef + k + 1), APF_FILTER_F32_DEFECT);
+  FilterCount fc;
+  fs.apply(k, Vb.as<T>(), AVb.as<T>(), lam, p, out.as<T>(), nullptr, nullptr, &fc);
+  stage_out<T>(ctx, n, p, out.as<T>(), ld, Y, ldy);
+}
+
+template <class T>
+void spmm_public(apf_ctx* ctx, const apf_matrix* A, const T* X, int64_t ldx, int64_t p, T* Y,
+                 int64_t ldy) {
+  const int64_t n = A->n, ld = block_ld(p);
+  DBuf Xb = stage_in<T>(ctx, n, p, X, ldx, ld);
+  DBuf out((size_t)n * ld * sizeof(T), ctx->stream, true);
+  spmm_plain<T>(ctx, A, Xb.as<T>(), ld, p, out.as<T>());
+  stage_out<T>(ctx, n, p, out.as<T>(), ld, Y, ldy);
+}
+
+template <class T>
+void cholqr2_public(apf_ctx* ctx, int64_t n, int64_t p, T* X, int64_t ldx) {
+  const int64_t ld = block_ld(p);
+  DBuf Xb = stage_in<T>(ctx, n, p, X, ldx, ld);
+  DBuf X1((size_t)n * ld * sizeof(T), ctx->stream, true);
+  SmallWork<T> sw;
+  sw.init(p, ctx->stream);
+  cholqr2_inplace<T>(ctx, n, p, Xb.as<T>(), X1.as<T>(), ld, sw);
+  stage_out<T>(ctx, n, p, Xb.as<T>(), ld, X, ldx);
+}
+
+template <class T>
+void rayleigh_ritz_public(apf_ctx* ctx, const apf_matrix* A, const T* Q, int64_t ldq, int64_t p,
+                          double* w, T* V, int64_t ldv) {
+  const int64_t n = A->n, ld = block_ld(p);
+  DBuf Qb = stage_in<T>(ctx, n, p, Q, ldq, ld);
+  DBuf AQ((size_t)n * ld * sizeof(T), ctx->stream, true);
+  DBuf Vb((size_t)n * ld * sizeof(T), ctx->stream, true);
+  SmallWork<T> sw;
+  sw.init(p, ctx->stream);
+  spmm_plain<T>(ctx, A, Qb.as<T>(), ld, p, AQ.as<T>());
+  gram<T>(ctx, n, p, p, Qb.as<T>(), ld, AQ.as<T>(), ld, sw.B, p, false);
+  symmetrize<T>(ctx, p, sw.B, p);
+  eigh_jacobi<T>(ctx, p, sw.B, p, w, sw.U, p);
+  gemm_tall<T>(ctx, n, p, p, Qb.as<T>(), ld, sw.U, p, Vb.as<T>(), ld, 1.0, 0.0, nullptr, ld, false);
+  const int derr = fetch_device_error(ctx);
+  if (derr == DEV_EIGH_NOCONV) throw ApfError{APF_ERR_EIGH, "eigh"};
+  if (derr == DEV_BARRIER_TIMEOUT) throw ApfError{APF_ERR_TIMEOUT, "eigh barrier"};
+  stage_out<T>(ctx, n, p, Vb.as<T>(), ld, V, ldv);
+}
+
+template <class T>
+void residual_norms_public(apf_ctx* ctx, const apf_matrix* A, const T* V, int64_t ldv, int64_t p,
+                           const double* w, double* host_out) {
+  const int64_t n = A->n, ld = block_ld(p);
+  DBuf Vb = stage_in<T>(ctx, n, p, V, ldv, ld);
+  DBuf AV((size_t)n * ld * sizeof(T), ctx->stream, true);
+  DBuf rd((size_t)p * sizeof(double), ctx->stream, false);
+  spmm_plain<T>(ctx, A, Vb.as<T>(), ld, p, AV.as<T>());
+  residual_norms<T>(ctx, n, p, AV.as<T>(), Vb.as<T>(), ld, w, rd.as<double>(), nullptr, 0.0);
+  APF_CUDA(cudaMemcpyAsync(host_out, rd.p, (size_t)p * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  APF_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+#define APF_INST(T)                                                                                  \
+  template void filter_apply_public<T>(apf_ctx*, const apf_matrix*, const double*, int, double,     \
+                                       double, int, const T*, int64_t, int64_t, T*, int64_t);       \
+  template void filter_apply_defect_public<T>(apf_ctx*, const apf_matrix*, const double*, int,      \
+                                              double, double, const T*, const T*, const double*,    \
+                                              int64_t, int64_t, T*, int64_t);                       \
+  template void spmm_public<T>(apf_ctx*, const apf_matrix*, const T*, int64_t, int64_t, T*,         \
+                               int64_t);                                                            \
+  template void cholqr2_public<T>(apf_ctx*, int64_t, int64_t, T*, int64_t);                         \
+  template void rayleigh_ritz_public<T>(apf_ctx*, const apf_matrix*, const T*, int64_t, int64_t,    \
+                                        double*, T*, int64_t);                                      \
+  template void residual_norms_public<T>(apf_ctx*, const apf_matrix*, const T*, int64_t, int64_t,   \
+                                         const double*, double*);
+APF_INST(double)
+APF_INST(double2)
+#undef APF_INST
+
+}  // namespace apf
