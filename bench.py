@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Benchmark: converged eigenpairs per second of AdaPolySI (Alg. 4) on GB300.
+
+A step is one complete solve (Lanczos bounds, coefficients, and every outer
+iteration: filter, CholQR2, Rayleigh-Ritz, residuals, spurious test, locking,
+degree selection) of the workload's interior eigenproblem, with the matrix
+already resident in HBM.  Default workload: the complex Hermitian 3D Anderson
+model on a 64^3 periodic grid (n = 262,144, random Peierls phases, disorder
+U[-2, 2]), interval [-0.0017, 0.0017] (about 100 eigenvalues), p = 160, FP32
+defect-corrected filter with FP64 orthogonalisation and Rayleigh-Ritz.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torch.distributed (one process per GPU): the ranks solve
+independent replicas (one interval: the path has no exchange step), time is
+the maximum over ranks and the value counts the eigenpairs of all ranks.
+The reference arm times the FP64 CPU oracle on a bounded sample (see
+``cpu_sample``).  One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "converged eigenpairs/s at residual 1e-10"
+UNIT = "eigenpairs/s"
+
+# Work of one solve of the default workload, as measured on a GB300 (iterations
+# and the sum over iterations of filter degree x active block width).  Used only
+# to scale the CPU oracle's bounded sample to a whole solve in the reference arm,
+# which runs without a GPU; the main arm uses the profile of its own solves.
+WORK_PROFILE = {"anderson3d_c_64": {"iterations": 30, "degree_width": 22.1e6, "eigenpairs": 99}}
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 complex
+# Clenshaw step on this workload (ncu, see profiles/); None until captured for
+# the current kernel.
+CLENSHAW_TRAFFIC_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="anderson3d_c_64")
+    ap.add_argument("--precision", default="f32_defect", choices=["f64", "f32", "f32_defect"])
+    ap.add_argument("--max-iter", type=int, default=60)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--filter-only", type=int, default=0,
+                    help="time only N applications of the filter kernel (degree --degree) instead of solves")
+    ap.add_argument("--degree", type=int, default=20)
+    return ap.parse_args()
+
+
+# ---- distributed plumbing ---------------------------------------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.on = self.world > 1
+        if self.on:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(self.local)
+            dist.init_process_group("nccl")
+            self.dist = dist
+
+    def barrier(self):
+        if self.on:
+            self.dist.barrier()
+
+    def reduce(self, x, op):
+        if not self.on:
+            return x
+        import torch
+        t = torch.tensor([float(x)], device="cuda", dtype=torch.float64)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self.reduce(x, self.dist.ReduceOp.MAX) if self.on else x
+
+    def sum(self, x):
+        return self.reduce(x, self.dist.ReduceOp.SUM) if self.on else x
+
+    def close(self):
+        if self.on:
+            self.dist.destroy_process_group()
+
+
+# ---- clocks during the timed region ------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        loaded = [s for s, p in zip(sm, power) if p is not None and p > 250.0] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": num(rows[0][2]), "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---- the CPU oracle's bounded sample -----------------------------------------------------
+
+def cpu_sample(workload: str, steps: int = 4):
+    """Time the oracle on a bounded sample of one solve of `workload`: `steps`
+    Clenshaw steps (Alg. 2) at the full block width and one orthogonalisation
+    + Rayleigh-Ritz + residual pass (CholQR2, Alg. 1).  Returns per-unit times."""
+    import numpy as np
+    from oracle import chebyshev as cb
+    from oracle import fsi
+    from oracle.filter import clenshaw_apply
+    from synth import rng, workloads
+    w = workloads.WORKLOADS[workload]()
+    A = w.matrix()
+    As = A.to_scipy()
+    V = rng.uniform_block(w.seed, rng.STREAM_INIT_BLOCK, A.n, w.p, A.is_complex)
+    coef = cb.filter_coefficients(-0.001, 0.001, steps)
+    t0 = time.perf_counter()
+    X = clenshaw_apply(As, coef, 0.18, 0.0, V)
+    t1 = time.perf_counter()
+    Q = fsi.cholqr2(X)
+    lam, Vr = fsi.rayleigh_ritz(As, Q)
+    fsi.residual_norms(As, Vr, lam)
+    t2 = time.perf_counter()
+    return dict(step_s=(t1 - t0) / steps, width=w.p, iter_s=t2 - t1, n=A.n,
+                cores=os.cpu_count(),
+                sample=f"{steps} Clenshaw steps (n={A.n}, width {w.p}) + 1 CholQR2/Rayleigh-Ritz/residual pass "
+                       f"of the oracle on the full {workload} matrix, scaled to one solve by its work profile")
+
+
+def cpu_eigenpairs_per_s(sample, profile):
+    t = (sample["step_s"] * profile["degree_width"] / sample["width"]
+         + sample["iter_s"] * profile["iterations"])
+    return profile["eigenpairs"] / t
+
+
+# ---- arms ----------------------------------------------------------------------------------
+
+def reference_arm(args, dist):
+    if dist.rank != 0:
+        return
+    prof = WORK_PROFILE[args.workload]
+    vals = []
+    sample = None
+    for i in range(args.warmup + args.steps):
+        sample = cpu_sample(args.workload, steps=2)
+        if i >= args.warmup:
+            vals.append(cpu_eigenpairs_per_s(sample, prof))
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": sample["cores"], "kind": "oracle",
+                             "sample": sample["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def ours_arm(args, dist):
+    import numpy as np
+    import torch
+    from paper_2604_00914_gb300 import binding as B
+    from synth import workloads
+
+    torch.cuda.set_device(dist.local)
+    stream = torch.cuda.current_stream()
+    w = workloads.WORKLOADS[args.workload]()
+    A = w.matrix()
+    ctx = B.Context(dist.local, stream=stream.cuda_stream)
+    M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
+    prec = {"f64": B.APF_FILTER_F64, "f32": B.APF_FILTER_F32, "f32_defect": B.APF_FILTER_F32_DEFECT}[args.precision]
+    prm = B.default_params(a=w.a, b=w.b, p=w.p, seed=w.seed + 1000 * dist.rank, filter_precision=prec,
+                           max_iter=args.max_iter)
+    peak, peak_kind = measured_peaks()
+
+    def one_solve():
+        r = B.solve(ctx, M, prm)
+        out = (r.count(), r.stats(), r.history())
+        r.close()
+        return out
+
+    if args.filter_only:
+        return filter_only(args, dist, B, ctx, M, A, w, peak, peak_kind)
+
+    for _ in range(args.warmup):
+        one_solve()
+    sampler = ClockSampler(dist.local)
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.launch_count()
+    ev0.record(stream)
+    eig = 0
+    fbytes = fms = 0.0
+    flaunch = 0
+    deg_width = 0.0
+    iters = 0
+    maxres = 0.0
+    for _ in range(args.steps):
+        e, st, hist = one_solve()
+        eig += e
+        fbytes += st["filter_bytes"]
+        fms += st["filter_kernel_ms"]
+        flaunch += st["filter_launches"]
+        deg_width += sum(h["degree"] * h["width"] for h in hist)
+        iters += st["iterations"]
+        maxres = max(maxres, st["max_residual"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop()
+    launches = ctx.launch_count() - launches0
+    ms_local = ev0.elapsed_time(ev1)
+    ms = dist.max(ms_local)
+    eig_all = dist.sum(eig)
+    value = eig_all / (ms / 1e3)
+
+    # end to end through the C ABI: host CSR in pinned memory -> solve -> eigenpairs to host
+    e2e = None
+    if not args.no_e2e:
+        rp = torch.from_numpy(A.rowptr).pin_memory()
+        ci = torch.from_numpy(A.colidx).pin_memory()
+        vv = torch.from_numpy(A.vals).pin_memory()
+        h2d = rp.numel() * 8 + ci.numel() * 4 + vv.numel() * vv.element_size()
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_tot = 0
+        d2h = 0
+        for _ in range(args.steps):
+            M2 = B.Matrix.from_csr(ctx, A.n, rp.numpy(), ci.numpy(), vv.numpy())
+            r = B.solve(ctx, M2, prm)
+            e = r.count()
+            lam = r.eigvals()
+            vecs = torch.empty((e, A.n), dtype=torch.complex128 if A.is_complex else torch.float64).pin_memory()
+            ctx.lib.check(ctx.lib.apf_result_eigvecs(r.h, vecs.data_ptr(), A.n, 0), ctx.h)
+            d2h = lam.nbytes + vecs.numel() * vecs.element_size()
+            e_tot += e
+            r.close()
+            M2.close()
+        torch.cuda.synchronize()
+        dt = dist.max(time.perf_counter() - t0)
+        e2e = {"value": dist.sum(e_tot) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if dist.rank == 0 and args.gpus == 1 and not args.no_cpu_baseline:
+        s = cpu_sample(args.workload, steps=4)
+        prof = {"iterations": iters / args.steps, "degree_width": deg_width / args.steps,
+                "eigenpairs": eig / args.steps}
+        cpu = {"value": cpu_eigenpairs_per_s(s, prof), "unit": UNIT, "cores": s["cores"], "kind": "oracle",
+               "sample": s["sample"].replace("its work profile", "the work profile of the timed GPU solves")}
+
+    achieved = fbytes / (fms * 1e-3) / 1e9 if fms > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "c128", "f32": "c64", "f32_defect": "c64+c128"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "p": w.p, "interval": [w.a, w.b],
+                   "precision": args.precision, "eigenpairs_per_solve": eig / args.steps,
+                   "iterations_per_solve": iters / args.steps, "max_residual": maxres,
+                   "l2": "inputs larger than L2 (blocks 335-671 MB)", "parallelism": f"replicas{args.gpus}"},
+        "roofline": {"kernel": "clenshaw_step (FP32 complex)", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": CLENSHAW_TRAFFIC_BYTES,
+                     "avg_launch_us": 1e3 * fms / flaunch if flaunch else None,
+                     "launches": flaunch},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    M.close()
+    ctx.close()
+
+
+def filter_only(args, dist, B, ctx, M, A, w, peak, peak_kind):
+    """Time N applications of the FP32 filter recurrence of degree `--degree` on
+    the workload's matrix and block width (the dominant kernel alone)."""
+    import numpy as np
+    import torch
+    from synth import rng
+    n, p = A.n, w.p
+    X = torch.from_numpy(rng.uniform_block(w.seed, rng.STREAM_INIT_BLOCK, n, p, A.is_complex)).cuda()
+    Y = torch.empty_like(X)
+    coef = np.linspace(1.0, 0.1, args.degree + 1)
+    for _ in range(args.warmup):
+        B.filter_apply(ctx, M, coef, 0.18, 0.0, X, Y, B.APF_FILTER_F32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.filter_only):
+        B.filter_apply(ctx, M, coef, 0.18, 0.0, X, Y, B.APF_FILTER_F32)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if dist.rank == 0:
+        print(json.dumps({"mode": "filter-only", "workload": args.workload, "degree": args.degree,
+                          "applications": args.filter_only, "seconds": dt}), flush=True)
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            reference_arm(args, dist)
+        else:
+            ours_arm(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

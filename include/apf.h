@@ -124,6 +124,7 @@ typedef struct {
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
  * to order all work on, or NULL for a stream owned by the context. */
 apf_status apf_create(apf_ctx** out, int device, void* cuda_stream);
+/* Destroy a context.  Destroy its matrices and results first: they refer to it. */
 apf_status apf_destroy(apf_ctx* ctx);
 const char* apf_status_string(int status);
 /* Text of the last error recorded on this context ("" if none). */

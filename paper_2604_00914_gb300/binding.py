@@ -176,9 +176,21 @@ class Context:
         h = C.c_void_p()
         self.lib.check(self.lib.apf_create(C.byref(h), int(device), stream))
         self.h = h
+        self._children = []
+
+    def _adopt(self, obj):
+        """Matrices and results must be freed before their context."""
+        import weakref
+        self._children = [r for r in self._children if r() is not None]
+        self._children.append(weakref.ref(obj))
 
     def close(self):
         if self.h:
+            for r in self._children:
+                o = r()
+                if o is not None:
+                    o.close()
+            self._children = []
             self.lib.apf_destroy(self.h)
             self.h = None
 
@@ -195,6 +207,7 @@ class Context:
 class Matrix:
     def __init__(self, ctx, h, n, dtype):
         self.ctx, self.h, self.n, self.dtype = ctx, h, n, dtype
+        ctx._adopt(self)
 
     @classmethod
     def from_csr(cls, ctx, n, rowptr, colidx, vals, on_device=False):
@@ -225,9 +238,9 @@ class Matrix:
         return cls(ctx, h, int(n), dt)
 
     def close(self):
-        if self.h:
+        if self.h and self.ctx.h:
             self.ctx.lib.apf_matrix_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -257,6 +270,7 @@ class Result:
 
     def __init__(self, ctx, h, status):
         self.ctx, self.h, self.status = ctx, h, status
+        ctx._adopt(self)
 
     def count(self):
         e = C.c_int64()
@@ -298,9 +312,9 @@ class Result:
         return [dict(zip(HISTORY_FIELDS, buf[6 * i:6 * i + 6])) for i in range(cnt.value)]
 
     def close(self):
-        if self.h:
+        if self.h and self.ctx.h:
             self.ctx.lib.apf_result_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

@@ -61,6 +61,17 @@ struct apf_matrix {
   int32_t* colidx = nullptr;     // device, nnz (every row holds its diagonal)
   void* vals = nullptr;          // device, nnz values (double or double2)
   double gersh_lo = 0, gersh_hi = 0;  // Gershgorin interval
+  // SELL-8 copy of the structure (rows in order, chunks of 8 rows padded to
+  // their longest row); sell_src maps a slot to its CSR entry (-1: padding)
+  bool sell_ok = false;
+  int sell_lmax = 0;
+  int64_t sell_slots = 0;
+  int64_t* sell_chunk_ptr = nullptr;
+  int32_t* sell_col = nullptr;
+  int32_t* sell_src = nullptr;
+  // autotuned Clenshaw-step shape per (element size, vectors per row):
+  // value = kind * 10000 + G * 100 + VPT, kind 1 = SELL, 0 = CSR
+  std::vector<std::pair<int64_t, int>> tune_cache;
 };
 
 namespace apf {
@@ -106,6 +117,26 @@ void clenshaw_step(apf_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
                    int64_t ncols, const typename ScalarTraits<T>::Real* coef_col,
                    typename ScalarTraits<T>::Real coef_scalar,
                    typename ScalarTraits<T>::Real alpha, T* Out);
+
+// SELL-8 form of the same step (A as sell_chunk_ptr / sell_col / sell values),
+// with the given (G, VPT) shape; see spmm_sell.cuh.
+template <class T, class TA>
+void clenshaw_step_sell(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* chunk_ptr,
+                        const int32_t* scol, const TA* sval, int lmax, const T* W, const T* Vin,
+                        const T* Y, int64_t ld, int64_t ncols,
+                        const typename ScalarTraits<T>::Real* coef_col,
+                        typename ScalarTraits<T>::Real coef_scalar,
+                        typename ScalarTraits<T>::Real alpha, T* Out);
+// CSR form with an explicit (G, VPT) shape (0, 0: automatic choice)
+template <class T, class TA>
+void clenshaw_step_shape(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* rowptr,
+                         const int32_t* colidx, const TA* vals, const T* W, const T* Vin, const T* Y,
+                         int64_t ld, int64_t ncols, const typename ScalarTraits<T>::Real* coef_col,
+                         typename ScalarTraits<T>::Real coef_scalar,
+                         typename ScalarTraits<T>::Real alpha, T* Out);
+// vals_sell[s] = src[s] >= 0 ? vals_csr[src[s]] : 0
+template <class TA>
+void sell_gather_values(apf_ctx* ctx, int64_t slots, const int32_t* src, const TA* csr, TA* out);
 
 // y = A x for one vector (Lanczos), FP64.
 template <class T>

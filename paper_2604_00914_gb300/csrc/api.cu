@@ -175,6 +175,41 @@ static void ingest_csr(apf_ctx* ctx, int64_t n, const std::vector<int64_t>& rp_i
   A->n = n;
   A->nnz = (int64_t)ci.size();
   A->dtype = dtype;
+  // SELL-8 structure (rows in order): used by the FP32 filter when the chunk
+  // padding costs at most half of the stored entries
+  const int CH = 8;
+  const int64_t nchunks = (n + CH - 1) / CH;
+  std::vector<int64_t> cptr((size_t)nchunks + 1, 0);
+  int lmax = 0;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    int64_t L = 0;
+    for (int64_t r = c * CH; r < std::min<int64_t>(n, (c + 1) * CH); ++r)
+      L = std::max<int64_t>(L, rp[(size_t)r + 1] - rp[(size_t)r]);
+    lmax = std::max<int>(lmax, (int)L);
+    cptr[(size_t)c + 1] = cptr[(size_t)c] + L * CH;
+  }
+  const int64_t slots = cptr[(size_t)nchunks];
+  const bool sell_ok = slots <= (int64_t)(1.5 * (double)A->nnz) && A->nnz < INT32_MAX && slots < INT32_MAX;
+  std::vector<int32_t> scol, ssrc;
+  if (sell_ok) {
+    scol.assign((size_t)slots, 0);
+    ssrc.assign((size_t)slots, -1);
+    for (int64_t c = 0; c < nchunks; ++c) {
+      const int64_t L = (cptr[(size_t)c + 1] - cptr[(size_t)c]) / CH;
+      for (int64_t r = c * CH; r < (c + 1) * CH; ++r) {
+        const int64_t len = r < n ? rp[(size_t)r + 1] - rp[(size_t)r] : 0;
+        for (int64_t t = 0; t < L; ++t) {
+          const size_t s = (size_t)(cptr[(size_t)c] + t * CH + (r - c * CH));
+          if (t < len) {
+            scol[s] = ci[(size_t)(rp[(size_t)r] + t)];
+            ssrc[s] = (int32_t)(rp[(size_t)r] + t);
+          } else {
+            scol[s] = (int32_t)(r < n ? r : 0);  // padding: the row itself, value 0
+          }
+        }
+      }
+    }
+  }
   try {
     APF_CUDA(cudaMalloc(&A->rowptr, rp.size() * sizeof(int64_t)));
     APF_CUDA(cudaMalloc(&A->colidx, std::max<size_t>(ci.size(), 1) * sizeof(int32_t)));
@@ -182,6 +217,17 @@ static void ingest_csr(apf_ctx* ctx, int64_t n, const std::vector<int64_t>& rp_i
     APF_CUDA(cudaMemcpyAsync(A->rowptr, rp.data(), rp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
     APF_CUDA(cudaMemcpyAsync(A->colidx, ci.data(), ci.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
     APF_CUDA(cudaMemcpyAsync(A->vals, vv.data(), vv.size() * sizeof(V), cudaMemcpyHostToDevice, ctx->stream));
+    if (sell_ok) {
+      A->sell_ok = true;
+      A->sell_lmax = lmax;
+      A->sell_slots = slots;
+      APF_CUDA(cudaMalloc(&A->sell_chunk_ptr, cptr.size() * sizeof(int64_t)));
+      APF_CUDA(cudaMalloc(&A->sell_col, std::max<size_t>(scol.size(), 1) * sizeof(int32_t)));
+      APF_CUDA(cudaMalloc(&A->sell_src, std::max<size_t>(ssrc.size(), 1) * sizeof(int32_t)));
+      APF_CUDA(cudaMemcpyAsync(A->sell_chunk_ptr, cptr.data(), cptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+      APF_CUDA(cudaMemcpyAsync(A->sell_col, scol.data(), scol.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+      APF_CUDA(cudaMemcpyAsync(A->sell_src, ssrc.data(), ssrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    }
     if (dtype == APF_C128)
       apf::gershgorin<double2>(ctx, n, A->rowptr, A->colidx, static_cast<const double2*>(A->vals), &A->gersh_lo, &A->gersh_hi);
     else
@@ -296,6 +342,9 @@ apf_status apf_matrix_destroy(apf_matrix* A) {
   if (A->rowptr) cudaFree(A->rowptr);
   if (A->colidx) cudaFree(A->colidx);
   if (A->vals) cudaFree(A->vals);
+  if (A->sell_chunk_ptr) cudaFree(A->sell_chunk_ptr);
+  if (A->sell_col) cudaFree(A->sell_col);
+  if (A->sell_src) cudaFree(A->sell_src);
   delete A;
   return APF_OK;
 }

@@ -1,6 +1,7 @@
 // FP32 instantiations of the Clenshaw step (real and complex), the filter
-// recurrence of APF_FILTER_F32 / APF_FILTER_F32_DEFECT.
-#include "spmm_impl.cuh"
+// recurrence of APF_FILTER_F32 / APF_FILTER_F32_DEFECT: the CSR kernel, the
+// SELL-8 kernel with TMA bulk staging, and the SELL value gather.
+#include "spmm_sell.cuh"
 
 namespace apf {
 
@@ -10,16 +11,60 @@ void clenshaw_step(apf_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
                    int64_t ncols, const typename ScalarTraits<T>::Real* coef_col,
                    typename ScalarTraits<T>::Real coef_scalar,
                    typename ScalarTraits<T>::Real alpha, T* Out) {
-  clenshaw_step_impl<T, TA>(ctx, n, rowptr, colidx, vals, W, Vin, Y, ld, ncols, coef_col,
+  clenshaw_step_impl<T, TA>(ctx, 0, 0, n, rowptr, colidx, vals, W, Vin, Y, ld, ncols, coef_col,
                             coef_scalar, alpha, Out);
 }
 
-template void clenshaw_step<float, float>(apf_ctx*, int64_t, const int64_t*, const int32_t*,
-                                          const float*, const float*, const float*, const float*,
-                                          int64_t, int64_t, const float*, float, float, float*);
-template void clenshaw_step<float2, float2>(apf_ctx*, int64_t, const int64_t*, const int32_t*,
-                                            const float2*, const float2*, const float2*,
-                                            const float2*, int64_t, int64_t, const float*, float,
-                                            float, float2*);
+template <class T, class TA>
+void clenshaw_step_shape(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* rowptr,
+                         const int32_t* colidx, const TA* vals, const T* W, const T* Vin, const T* Y,
+                         int64_t ld, int64_t ncols, const typename ScalarTraits<T>::Real* coef_col,
+                         typename ScalarTraits<T>::Real coef_scalar,
+                         typename ScalarTraits<T>::Real alpha, T* Out) {
+  clenshaw_step_impl<T, TA>(ctx, G, VPT, n, rowptr, colidx, vals, W, Vin, Y, ld, ncols, coef_col,
+                            coef_scalar, alpha, Out);
+}
+
+template <class T, class TA>
+void clenshaw_step_sell(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* chunk_ptr,
+                        const int32_t* scol, const TA* sval, int lmax, const T* W, const T* Vin,
+                        const T* Y, int64_t ld, int64_t ncols,
+                        const typename ScalarTraits<T>::Real* coef_col,
+                        typename ScalarTraits<T>::Real coef_scalar,
+                        typename ScalarTraits<T>::Real alpha, T* Out) {
+  clenshaw_sell_launch<T, TA>(ctx, G, VPT, n, chunk_ptr, scol, sval, lmax, W, Vin, Y, ld, ncols,
+                              coef_col, coef_scalar, alpha, Out);
+}
+
+template <class TA>
+__global__ void k_sell_gather(int64_t slots, const int32_t* __restrict__ src, const TA* __restrict__ csr,
+                              TA* __restrict__ out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= slots) return;
+  const int32_t e = src[s];
+  out[s] = e >= 0 ? csr[e] : szero<TA>();
+}
+
+template <class TA>
+void sell_gather_values(apf_ctx* ctx, int64_t slots, const int32_t* src, const TA* csr, TA* out) {
+  if (slots == 0) return;
+  k_sell_gather<TA><<<(unsigned)((slots + 255) / 256), 256, 0, ctx->stream>>>(slots, src, csr, out);
+  count_launch(ctx);
+}
+
+#define APF_INST32(T)                                                                                 \
+  template void clenshaw_step<T, T>(apf_ctx*, int64_t, const int64_t*, const int32_t*, const T*,      \
+                                    const T*, const T*, const T*, int64_t, int64_t, const float*,     \
+                                    float, float, T*);                                                \
+  template void clenshaw_step_shape<T, T>(apf_ctx*, int, int, int64_t, const int64_t*,                \
+                                          const int32_t*, const T*, const T*, const T*, const T*,     \
+                                          int64_t, int64_t, const float*, float, float, T*);          \
+  template void clenshaw_step_sell<T, T>(apf_ctx*, int, int, int64_t, const int64_t*, const int32_t*, \
+                                         const T*, int, const T*, const T*, const T*, int64_t,        \
+                                         int64_t, const float*, float, float, T*);                    \
+  template void sell_gather_values<T>(apf_ctx*, int64_t, const int32_t*, const T*, T*);
+APF_INST32(float)
+APF_INST32(float2)
+#undef APF_INST32
 
 }  // namespace apf

@@ -11,7 +11,7 @@ void clenshaw_step(apf_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
                    int64_t ncols, const typename ScalarTraits<T>::Real* coef_col,
                    typename ScalarTraits<T>::Real coef_scalar,
                    typename ScalarTraits<T>::Real alpha, T* Out) {
-  clenshaw_step_impl<T, TA>(ctx, n, rowptr, colidx, vals, W, Vin, Y, ld, ncols, coef_col,
+  clenshaw_step_impl<T, TA>(ctx, 0, 0, n, rowptr, colidx, vals, W, Vin, Y, ld, ncols, coef_col,
                             coef_scalar, alpha, Out);
 }
 

@@ -13,6 +13,7 @@
 
 #include "host_math.h"
 #include "solver.h"
+#include "spmm_impl.cuh"
 
 namespace apf {
 
@@ -110,13 +111,105 @@ static double step_bytes(int64_t n, int64_t nnz, int64_t p, size_t sval, size_t 
   return mat + streams * (double)n * (double)p * (double)sblk;
 }
 
+// One Clenshaw step of the chosen kernel: CSR or SELL-8 storage of A_hat and
+// the (G, VPT) shape picked by the autotuner.
+template <class S>
+struct Stepper {
+  using Real = typename ScalarTraits<S>::Real;
+  apf_ctx* ctx = nullptr;
+  const apf_matrix* A = nullptr;
+  const S* csr_vals = nullptr;   // A_hat values in CSR order
+  const S* sell_vals = nullptr;  // A_hat values in SELL-8 order (FP32 only), or null
+  int64_t ld = 0;
+  int kind = 0, G = 0, VPT = 0;  // kind 1: SELL
+  void operator()(const S* W, const S* Vin, const S* Y, int64_t ncols, const Real* coef_col,
+                  Real coef_scalar, Real alpha, S* Out) const {
+    if (kind == 1) {
+      if constexpr (sizeof(Real) == 4)
+        clenshaw_step_sell<S, S>(ctx, G, VPT, A->n, A->sell_chunk_ptr, A->sell_col, sell_vals,
+                                 A->sell_lmax, W, Vin, Y, ld, ncols, coef_col, coef_scalar, alpha, Out);
+    } else if (G > 0) {
+      if constexpr (sizeof(Real) == 4)
+        clenshaw_step_shape<S, S>(ctx, G, VPT, A->n, A->rowptr, A->colidx, csr_vals, W, Vin, Y, ld,
+                                  ncols, coef_col, coef_scalar, alpha, Out);
+    } else {
+      clenshaw_step<S, S>(ctx, A->n, A->rowptr, A->colidx, csr_vals, W, Vin, Y, ld, ncols, coef_col,
+                          coef_scalar, alpha, Out);
+    }
+  }
+};
+
+// Autotuner: time each candidate shape on the live buffers (one warm-up and
+// three timed launches) and keep the fastest per (element size, ld, width) in
+// the matrix.  All shapes do the same arithmetic in the same order, so the
+// choice changes the time, never the result.
+template <class S>
+static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, const S* Yb, S* Ob) {
+  using Real = typename ScalarTraits<S>::Real;
+  constexpr int E = ScalarTraits<S>::per16;
+  st.kind = 0;
+  st.G = st.VPT = 0;
+  if constexpr (sizeof(Real) != 4) return;
+  const int nvec = (int)((p + E - 1) / E);
+  apf_matrix* A = const_cast<apf_matrix*>(st.A);
+  const int64_t key = ((int64_t)sizeof(S) << 48) | ((int64_t)st.ld << 16) | nvec;
+  for (auto& kv : A->tune_cache)
+    if (kv.first == key) {
+      st.kind = kv.second / 10000;
+      st.G = (kv.second / 100) % 100;
+      st.VPT = kv.second % 100;
+      return;
+    }
+  struct Cand { int kind, G, VPT; };
+  std::vector<Cand> cands;
+  int g0, v0;
+  choose_group(nvec > 256 ? 256 : nvec, &g0, &v0);
+  cands.push_back({0, g0, v0});
+  if (A->sell_ok && nvec <= 256) {
+    static const int shapes[][2] = {{8, 1}, {8, 2}, {8, 3}, {8, 4}, {16, 2}, {16, 3}, {16, 4}, {16, 5},
+                                    {16, 6}, {32, 2}, {32, 3}, {32, 4}, {32, 5}, {32, 6}, {32, 8}};
+    for (auto& sh : shapes) {
+      const int g = sh[0], v = sh[1];
+      if (g * v < nvec) continue;
+      if ((double)(g * v - nvec) / (g * v) > 0.4) continue;
+      const int R = 256 / g;
+      if ((size_t)R * st.ld * sizeof(S) * 2 + (size_t)R * A->sell_lmax * 12 > 180 * 1024) continue;
+      cands.push_back({1, g, v});
+    }
+  }
+  cudaEvent_t e0, e1;
+  APF_CUDA(cudaEventCreate(&e0));
+  APF_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  Cand pick = cands[0];
+  for (const Cand& c : cands) {
+    Stepper<S> t = st;
+    t.kind = c.kind;
+    t.G = c.G;
+    t.VPT = c.VPT;
+    t(Wb, Vb, Yb, p, nullptr, (Real)0.5, (Real)2, Ob);
+    APF_CUDA(cudaEventRecord(e0, st.ctx->stream));
+    for (int r = 0; r < 3; ++r) t(Wb, Vb, Yb, p, nullptr, (Real)0.5, (Real)2, Ob);
+    APF_CUDA(cudaEventRecord(e1, st.ctx->stream));
+    APF_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    APF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) { best = ms; pick = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  st.kind = pick.kind;
+  st.G = pick.G;
+  st.VPT = pick.VPT;
+  A->tune_cache.push_back({key, pick.kind * 10000 + pick.G * 100 + pick.VPT});
+}
+
 // Plain form: returns the buffer (B1 or B2) that holds rho(A_hat) Y.
 // a: host coefficients a_0..a_k.  ev0/ev1 bracket the SpMM launches.
 template <class S>
-static S* clenshaw_plain(apf_ctx* ctx, int64_t n, int64_t nnz, const int64_t* rowptr,
-                         const int32_t* colidx, const S* Ahat, const S* Y, int64_t ld, int64_t p,
-                         const double* a, int k, S* B1, S* B2, cudaEvent_t ev0, cudaEvent_t ev1,
-                         FilterCount* fc) {
+static S* clenshaw_plain(apf_ctx* ctx, const Stepper<S>& step, int64_t n, int64_t nnz, const S* Y,
+                         int64_t ld, int64_t p, const double* a, int k, S* B1, S* B2, cudaEvent_t ev0,
+                         cudaEvent_t ev1, FilterCount* fc) {
   using Real = typename ScalarTraits<S>::Real;
   if (k == 0) {
     scale_block<S>(ctx, n, p, a[0], Y, ld, B1, ld);
@@ -130,7 +223,7 @@ static S* clenshaw_plain(apf_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
   for (int j = k - 1; j >= 0; --j) {
     S* out = P2 ? P2 : (P1 == B1 ? B2 : B1);
     const Real alpha = (j == 0) ? (Real)1 : (Real)2;
-    clenshaw_step<S, S>(ctx, n, rowptr, colidx, Ahat, P1, P2, Y, ld, p, nullptr, (Real)a[j], alpha, out);
+    step(P1, P2, Y, p, nullptr, (Real)a[j], alpha, out);
     fc->launches += 1;
     fc->bytes += step_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr, true);
     P2 = P1;
@@ -143,10 +236,9 @@ static S* clenshaw_plain(apf_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
 // Defect form: returns the buffer holding D (nullptr when D = 0, i.e. k = 0).
 // F: device per-column coefficients, row j at F + j ld (see defect_coefficients).
 template <class S>
-static S* clenshaw_defect(apf_ctx* ctx, int64_t n, int64_t nnz, const int64_t* rowptr,
-                          const int32_t* colidx, const S* Ahat, const S* R, int64_t ld, int64_t p,
-                          const float* F, int k, S* B1, S* B2, cudaEvent_t ev0, cudaEvent_t ev1,
-                          FilterCount* fc) {
+static S* clenshaw_defect(apf_ctx* ctx, const Stepper<S>& step, int64_t n, int64_t nnz, const S* R,
+                          int64_t ld, int64_t p, const float* F, int k, S* B1, S* B2, cudaEvent_t ev0,
+                          cudaEvent_t ev1, FilterCount* fc) {
   if (k == 0) {
     if (ev0) { APF_CUDA(cudaEventRecord(ev0, ctx->stream)); APF_CUDA(cudaEventRecord(ev1, ctx->stream)); }
     return nullptr;
@@ -163,8 +255,7 @@ static S* clenshaw_defect(apf_ctx* ctx, int64_t n, int64_t nnz, const int64_t* r
   for (int j = k - 2; j >= 0; --j) {
     S* out = P2 ? P2 : (P1 == B1 ? B2 : B1);
     const float alpha = (j == 0) ? 1.0f : 2.0f;
-    clenshaw_step<S, S>(ctx, n, rowptr, colidx, Ahat, P1, P2, R, ld, p, F + (int64_t)j * ld, 0.0f,
-                        alpha, out);
+    step(P1, P2, R, p, F + (int64_t)j * ld, 0.0f, alpha, out);
     fc->launches += 1;
     fc->bytes += step_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr, true);
     P2 = P1;
@@ -182,11 +273,11 @@ struct FilterState {
   const apf_matrix* A = nullptr;
   int64_t n = 0, ld = 0;
   double l1 = 0, l2 = 0;
-  DBuf Ahat64, Ahat32;     // l1 A + l2 I in FP64 / FP32
-  DBuf B1, B2, Y32;        // recurrence buffers
-  DBuf coef_dev;           // a_j on the device (defect form)
-  DBuf F, rho;             // defect coefficients
-  std::vector<double> a;   // host a_j
+  DBuf Ahat64, Ahat32, Asell32;  // l1 A + l2 I in FP64 / FP32 (CSR and SELL-8 order)
+  DBuf B1, B2, Y32;              // recurrence buffers
+  DBuf coef_dev;                 // a_j on the device (defect form)
+  DBuf F, rho;                   // defect coefficients
+  std::vector<double> a;         // host a_j
   int precision = APF_FILTER_F64;
   int kmax = 0;
 
@@ -210,6 +301,10 @@ struct FilterState {
     } else {
       Ahat32.alloc((size_t)A->nnz * sizeof(TL), ctx->stream, false);
       scale_shift_matrix<T, TL>(ctx, n, A->rowptr, A->colidx, vals, l1, l2, Ahat32.as<TL>());
+      if (A->sell_ok) {
+        Asell32.alloc((size_t)A->sell_slots * sizeof(TL), ctx->stream, false);
+        sell_gather_values<TL>(ctx, A->sell_slots, A->sell_src, Ahat32.as<TL>(), Asell32.as<TL>());
+      }
       B1.alloc((size_t)n * ld * sizeof(TL), ctx->stream, true);
       B2.alloc((size_t)n * ld * sizeof(TL), ctx->stream, true);
       Y32.alloc((size_t)n * ld * sizeof(TL), ctx->stream, true);
@@ -221,6 +316,27 @@ struct FilterState {
     }
   }
 
+  Stepper<T> stepper64() const {
+    Stepper<T> s;
+    s.ctx = ctx;
+    s.A = A;
+    s.csr_vals = Ahat64.as<T>();
+    s.ld = ld;
+    return s;
+  }
+
+  // the tuned FP32 stepper for width p (tuning overwrites B1: call before use)
+  Stepper<TL> stepper32(int64_t p) {
+    Stepper<TL> s;
+    s.ctx = ctx;
+    s.A = A;
+    s.csr_vals = Ahat32.as<TL>();
+    s.sell_vals = A->sell_ok ? Asell32.as<TL>() : nullptr;
+    s.ld = ld;
+    tune_stepper<TL>(s, p, Y32.as<TL>(), B2.as<TL>(), Y32.as<TL>(), B1.as<TL>());
+    return s;
+  }
+
   // X = rho(A_hat) V with degree k; V, X: n x p (ld).  For the defect form AV
   // and lam (device) hold A V and the Ritz values of V; pass nullptr to use the
   // plain FP32 recurrence instead.
@@ -229,24 +345,25 @@ struct FilterState {
     APF_REQUIRE(k <= kmax, APF_ERR_ARG);
     const int64_t nnz = A->nnz;
     if (precision == APF_FILTER_F64) {
-      T* out = clenshaw_plain<T>(ctx, n, nnz, A->rowptr, A->colidx, Ahat64.as<T>(), V, ld, p,
-                                 a.data(), k, B1.as<T>(), B2.as<T>(), ev0, ev1, fc);
+      T* out = clenshaw_plain<T>(ctx, stepper64(), n, nnz, V, ld, p, a.data(), k, B1.as<T>(),
+                                 B2.as<T>(), ev0, ev1, fc);
       copy_block<T>(ctx, n, p, out, ld, X, ld);
       return;
     }
+    const Stepper<TL> st = stepper32(p);
     if (precision == APF_FILTER_F32_DEFECT && AV != nullptr && lam != nullptr) {
       // R_hat = l1 (A V - V diag(lam)) in FP32; norms are not needed here
       DBuf scratch((size_t)p * sizeof(double), ctx->stream, false);
       residual_norms<T>(ctx, n, p, AV, V, ld, lam, scratch.as<double>(), Y32.as<TL>(), l1);
       defect_coefficients(ctx, p, ld, k, coef_dev.as<double>(), lam, l1, l2, F.as<float>(), rho.as<double>());
-      TL* D = clenshaw_defect<TL>(ctx, n, nnz, A->rowptr, A->colidx, Ahat32.as<TL>(), Y32.as<TL>(),
-                                  ld, p, F.as<float>(), k, B1.as<TL>(), B2.as<TL>(), ev0, ev1, fc);
+      TL* D = clenshaw_defect<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, p, F.as<float>(), k, B1.as<TL>(),
+                                  B2.as<TL>(), ev0, ev1, fc);
       defect_combine<T>(ctx, n, p, V, ld, rho.as<double>(), D, ld, X, ld);
       return;
     }
     cast_block<T, TL>(ctx, n, p, V, ld, Y32.as<TL>(), ld);
-    TL* out = clenshaw_plain<TL>(ctx, n, nnz, A->rowptr, A->colidx, Ahat32.as<TL>(), Y32.as<TL>(),
-                                 ld, p, a.data(), k, B1.as<TL>(), B2.as<TL>(), ev0, ev1, fc);
+    TL* out = clenshaw_plain<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, p, a.data(), k, B1.as<TL>(),
+                                 B2.as<TL>(), ev0, ev1, fc);
     cast_block<TL, T>(ctx, n, p, out, ld, X, ld);
   }
 };

@@ -143,7 +143,7 @@ inline void choose_group(int nvec, int* G, int* VPT) {
   }
 
 template <class T, class TA>
-void clenshaw_step_impl(apf_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* colidx,
+void clenshaw_step_impl(apf_ctx* ctx, int Gsel, int Vsel, int64_t n, const int64_t* rowptr, const int32_t* colidx,
                         const TA* vals, const T* W, const T* Vin, const T* Y, int64_t ld,
                         int64_t ncols, const typename ScalarTraits<T>::Real* coef_col,
                         typename ScalarTraits<T>::Real coef_scalar,
@@ -160,6 +160,7 @@ void clenshaw_step_impl(apf_ctx* ctx, int64_t n, const int64_t* rowptr, const in
     const int64_t c0 = v0 * E;
     int G, VPT;
     choose_group(nv, &G, &VPT);
+    if (Gsel > 0 && Vsel > 0 && Gsel * Vsel >= nv) { G = Gsel; VPT = Vsel; }
     const int64_t rows_per_block = 256 / G;
     const unsigned grid = (unsigned)((n + rows_per_block - 1) / rows_per_block);
     bool launched = false;

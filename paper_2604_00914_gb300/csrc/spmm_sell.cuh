@@ -1,0 +1,240 @@
+// The Clenshaw step on the SELL-8 layout with TMA bulk-copy staging.
+//
+// Layout (built at ingest, SELL-C-sigma with C = 8, sigma = 1: rows keep their
+// order): chunk c holds rows 8c..8c+7, padded to the chunk's longest row;
+// entry t of row r sits at chunk_ptr[c] + 8 t + (r mod 8).  Padding entries
+// point at the row itself with value 0, so they add exact zeros.
+//
+// A CTA owns R = 256 / G consecutive rows, i.e. R / 8 whole chunks whose
+// entries are one contiguous range.  At kernel start one thread issues
+// cp.async.bulk copies (TMA, completion on an mbarrier) of that range's
+// column indices and values and of the CTA's rows of Y and Vin (contiguous,
+// row-major) into shared memory; the rows of W are then gathered into
+// registers (neighbouring rows of a banded matrix hit in L2) while the copies
+// are in flight, and the epilogue reads Y and Vin from shared memory.  The
+// dependent chain per row is thus: one round for the structure (overlapped
+// with the Y / Vin staging), the gathers, the store.
+//
+// Every wait on the mbarrier is bounded in time; on expiry the kernel records
+// DEV_BARRIER_TIMEOUT, waits (bounded) for its copies and returns.
+#pragma once
+#include "spmm_impl.cuh"
+
+namespace apf {
+
+constexpr int SELL_C = 8;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ uint64_t sell_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for phase 0 of the CTA's barrier.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, 0)) return true;
+  const uint64_t t0 = sell_ns();
+  while (!mbar_try_wait(bar, 0)) {
+    if (sell_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+// shared-memory bytes of one CTA: barrier, staged Y and Vin rows, structure
+inline size_t sell_smem_bytes(int R, int64_t ld, size_t sT, int lmax, size_t sTA, bool y, bool vin) {
+  size_t b = 128;
+  b += (y ? (size_t)R * ld * sT : 0) + (vin ? (size_t)R * ld * sT : 0);
+  b += (size_t)R * lmax * 4;
+  b = (b + 15) / 16 * 16;
+  b += (size_t)R * lmax * sTA;
+  b += (size_t)(R / SELL_C + 1) * 8 + 16;
+  return b;
+}
+
+template <class T, class TA, int G, int VPT>
+__global__ void __launch_bounds__(256, (VPT <= 4 ? 4 : (VPT <= 6 ? 3 : 2)))
+k_clenshaw_sell(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32_t* __restrict__ scol,
+                const TA* __restrict__ sval, int lmax, const T* __restrict__ W, const T* Vin,
+                const T* __restrict__ Y, int64_t ld, int nvec,
+                const typename ScalarTraits<T>::Real* __restrict__ coef_col,
+                typename ScalarTraits<T>::Real coef_scalar, typename ScalarTraits<T>::Real alpha, T* Out,
+                int* err) {
+  using Real = typename ScalarTraits<T>::Real;
+  constexpr int E = ScalarTraits<T>::per16;
+  constexpr int R = 256 / G;
+  constexpr int NCH = R / SELL_C;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  T* Ys = reinterpret_cast<T*>(smem + 128);
+  T* Vs = Ys + (Y ? (int64_t)R * ld : 0);
+  int32_t* cols = reinterpret_cast<int32_t*>(Vs + (Vin ? (int64_t)R * ld : 0));
+  size_t voff = (size_t)((unsigned char*)(cols + R * lmax) - smem);
+  voff = (voff + 15) / 16 * 16;
+  TA* vals = reinterpret_cast<TA*>(smem + voff);
+  int64_t* cps = reinterpret_cast<int64_t*>(vals + R * lmax);
+
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int nr = (int)((n - r0) < R ? (n - r0) : R);
+  const int64_t c0 = r0 / SELL_C;
+  const int nch = (nr + SELL_C - 1) / SELL_C;
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    uint32_t yv = 0;
+    if (Y) yv += (uint32_t)((int64_t)nr * ld * sizeof(T));
+    if (Vin) yv += (uint32_t)((int64_t)nr * ld * sizeof(T));
+    if (yv) mbar_expect_tx(bar, yv);
+    if (Y) bulk_g2s(Ys, Y + r0 * ld, (uint32_t)((int64_t)nr * ld * sizeof(T)), bar);
+    if (Vin) bulk_g2s(Vs, Vin + r0 * ld, (uint32_t)((int64_t)nr * ld * sizeof(T)), bar);
+    for (int c = 0; c <= nch; ++c) cps[c] = chunk_ptr[c0 + c];
+    const int64_t e0 = cps[0], e1 = cps[nch];
+    const uint32_t nc = (uint32_t)((e1 - e0) * 4), nv = (uint32_t)((e1 - e0) * sizeof(TA));
+    mbar_expect_tx(bar, nc + nv);
+    bulk_g2s(cols, scol + e0, nc, bar);
+    bulk_g2s(vals, sval + e0, nv, bar);
+    mbar_arrive(bar);
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(bar, 1000000000ull)) {
+    atomicCAS(err, 0, DEV_BARRIER_TIMEOUT);
+    mbar_wait_bounded(bar, 1000000000ull);  // let the copies land before leaving
+    return;
+  }
+  (void)NCH;
+
+  const int lane = threadIdx.x % G;
+  const int rl = threadIdx.x / G;  // local row
+  if (rl >= nr) return;
+  const int64_t row = r0 + rl;
+  const int cl = rl / SELL_C, rr = rl % SELL_C;
+  const int64_t base = cps[cl] - cps[0];
+  const int len = (int)((cps[cl + 1] - cps[cl]) / SELL_C);
+
+  T acc[VPT][E];
+#pragma unroll
+  for (int q = 0; q < VPT; ++q)
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[q][e] = szero<T>();
+
+#pragma unroll 4
+  for (int t = 0; t < len; ++t) {
+    const int64_t s = base + (int64_t)t * SELL_C + rr;
+    const int col = cols[s];
+    const TA v = vals[s];
+    const uint4* wrow = reinterpret_cast<const uint4*>(W + (int64_t)col * ld);
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) {
+      const int vi = lane + q * G;
+      if (vi < nvec) {
+        Pack16<T> w;
+        w.u = __ldg(wrow + vi);
+#pragma unroll
+        for (int e = 0; e < E; ++e) madd(acc[q][e], v, w.t[e]);
+      }
+    }
+  }
+  const T* ys = Ys + (int64_t)rl * ld;
+  const T* vs = Vs + (int64_t)rl * ld;
+#pragma unroll
+  for (int q = 0; q < VPT; ++q) {
+    const int vi = lane + q * G;
+    if (vi >= nvec) continue;
+    Pack16<T> y, v, o;
+    if (Y) y.u = reinterpret_cast<const uint4*>(ys)[vi];
+    if (Vin) v.u = reinterpret_cast<const uint4*>(vs)[vi];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      T r = rmul(alpha, acc[q][e]);
+      if (Vin) r = sub(r, v.t[e]);
+      if (Y) {
+        const Real f = coef_col ? coef_col[vi * E + e] : coef_scalar;
+        r = add(r, rmul(f, y.t[e]));
+      }
+      o.t[e] = r;
+    }
+    reinterpret_cast<uint4*>(Out + row * ld)[vi] = o.u;
+  }
+}
+
+// The (G, VPT) shapes compiled for the SELL kernel.
+struct SellShape {
+  int G, VPT;
+};
+static const SellShape kSellShapes[] = {{8, 1}, {8, 2}, {8, 3}, {8, 4}, {16, 2}, {16, 3}, {16, 4},
+                                        {16, 5}, {16, 6}, {32, 2}, {32, 3}, {32, 4}, {32, 5}, {32, 6},
+                                        {32, 8}};
+
+template <class T, class TA>
+void clenshaw_sell_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* chunk_ptr,
+                          const int32_t* scol, const TA* sval, int lmax, const T* W, const T* Vin,
+                          const T* Y, int64_t ld, int64_t ncols,
+                          const typename ScalarTraits<T>::Real* coef_col,
+                          typename ScalarTraits<T>::Real coef_scalar,
+                          typename ScalarTraits<T>::Real alpha, T* Out) {
+  constexpr int E = ScalarTraits<T>::per16;
+  APF_REQUIRE(ld % E == 0 && W != Out, APF_ERR_ARG);
+  if (n == 0 || ncols == 0) return;
+  const int nvec = (int)((ncols + E - 1) / E);
+  APF_REQUIRE(nvec <= G * VPT, APF_ERR_ARG);
+  const int R = 256 / G;
+  const size_t smem = sell_smem_bytes(R, ld, sizeof(T), lmax, sizeof(TA), Y != nullptr, Vin != nullptr);
+  APF_REQUIRE(smem <= 200 * 1024, APF_ERR_ARG);
+  const unsigned grid = (unsigned)((n + R - 1) / R);
+  bool launched = false;
+#define APF_SELL_CASE(GG, VV)                                                                        \
+  if (G == GG && VPT == VV) {                                                                        \
+    auto kern = k_clenshaw_sell<T, TA, GG, VV>;                                                      \
+    static bool attr_set = false;                                                                    \
+    if (!attr_set) {                                                                                 \
+      APF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); \
+      attr_set = true;                                                                               \
+    }                                                                                                \
+    kern<<<grid, 256, smem, ctx->stream>>>(n, chunk_ptr, scol, sval, lmax, W, Vin, Y, ld, nvec,      \
+                                           coef_col, coef_scalar, alpha, Out, ctx->d_err);           \
+    launched = true;                                                                                 \
+  }
+  APF_SELL_CASE(8, 1) APF_SELL_CASE(8, 2) APF_SELL_CASE(8, 3) APF_SELL_CASE(8, 4)
+  APF_SELL_CASE(16, 2) APF_SELL_CASE(16, 3) APF_SELL_CASE(16, 4) APF_SELL_CASE(16, 5) APF_SELL_CASE(16, 6)
+  APF_SELL_CASE(32, 2) APF_SELL_CASE(32, 3) APF_SELL_CASE(32, 4) APF_SELL_CASE(32, 5) APF_SELL_CASE(32, 6)
+  APF_SELL_CASE(32, 8)
+#undef APF_SELL_CASE
+  APF_REQUIRE(launched, APF_ERR_ARG);
+  count_launch(ctx);
+}
+
+}  // namespace apf

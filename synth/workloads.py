@@ -86,7 +86,19 @@ def anderson3d_c_64() -> Workload:
                     "3D Anderson 64^3 periodic, Peierls phases, W=4, complex, p=160")
 
 
+def anderson3d_c_48() -> Workload:
+    """The 64^3 workload's model on a 48^3 grid (n = 110,592), p = 160: a
+    smaller case for kernel profiling whose blocks (141 MB in FP32 complex)
+    still exceed L2."""
+    h = ANDERSON64_HALFWIDTH
+    return Workload("anderson3d_c_48", BASE_SEED + 11, 160, -h, h, True,
+                    "3D Anderson 48^3 periodic, Peierls phases, W=4, complex, p=160")
+
+
+_BUILDERS["anderson3d_c_48"] = lambda seed: matrices.anderson(48, 3, 4.0, seed, complex_phases=True)
+
 WORKLOADS = {
     "lap2d_32": lap2d_32,
     "anderson3d_c_64": anderson3d_c_64,
+    "anderson3d_c_48": anderson3d_c_48,
 }

@@ -113,10 +113,15 @@ def test_ks_like_small_low_end(B, ctx, prec):
 def test_fixed_jackson_degree(B, ctx):
     A = matrices.anderson(9, 3, 3.0, 2, False)
     lam = np.linalg.eigvalsh(A.to_dense())
-    a, b = _interval_around(lam, -1.0, 6)
-    out = _solve(B, ctx, A, a, b, 16, 2, k_fixed=120, damping=B.APF_DAMP_JACKSON)
+    a, b = _interval_around(lam, -1.5, 5)
+    out = _solve(B, ctx, A, a, b, 20, 2, k_fixed=250, damping=B.APF_DAMP_JACKSON)
     _check(out, A, lam[(lam >= a) & (lam <= b)])
-    assert all(int(h["degree"]) == 120 for h in out["hist"])
+    assert all(int(h["degree"]) == 250 for h in out["hist"])
+    # the oracle converges in the same number of iterations from the same start
+    V0 = rng.uniform_block(2, rng.STREAM_INIT_BLOCK, A.n, 20, False)
+    v0 = rng.uniform_block(2, rng.STREAM_LANCZOS, A.n, 1, False)[:, 0]
+    ro = fsi.adapolysi(A.to_scipy(), a, b, fsi.Params(p=20, k_fixed=250, damping=cb.DAMP_JACKSON), V0, v0)
+    assert ro.stats["iterations"] == out["stats"]["iterations"]
 
 
 def _stall_matrix(seed):
