@@ -250,6 +250,25 @@ apf_status apf_rayleigh_ritz(apf_ctx* ctx, const apf_matrix* A, const void* Q, i
 apf_status apf_residual_norms(apf_ctx* ctx, const apf_matrix* A, const void* V, int64_t ld,
                               int64_t p, const double* w, double* host_out);
 
+/* G = X^H Y exactly as apf_gram computes it, for callers that cannot allocate
+ * device memory (code inside a CUDA graph being captured, an allocator's own
+ * callbacks, a host with a fixed memory budget).  The paper has no
+ * counterpart: this is a deployment variant of the Gram step.
+ * It takes no context and allocates nothing: the partial sums of its row
+ * splits live in one file-scope device array of 8 MiB that every GPU loading
+ * the library holds until the process exits.  Limits: pa * pb elements of
+ * `dtype` must fit in 8 MiB (pa = pb <= 1024 real, <= 724 complex), else
+ * APF_ERR_ARG.  X, Y, G: device pointers on the current device; work is
+ * ordered on `cuda_stream` (a cudaStream_t, NULL for the legacy default
+ * stream).  The first call on each device looks up the array's device address
+ * with cudaGetSymbolAddress while that device is current: make that first
+ * call before any stream capture.  All calls on a device share the array and
+ * it keeps the last call's contents (no call needs it cleared); calls whose
+ * work overlaps on the GPU (different streams, no ordering) race on it. */
+apf_status apf_gram_noalloc(int32_t dtype, int64_t n, int64_t pa, int64_t pb, const void* X,
+                            int64_t ldx, const void* Y, int64_t ldy, void* G, int64_t ldg,
+                            void* cuda_stream);
+
 /* The seeded initial block: entry (i, c) uniform in [-1, 1) from counter-based
  * SplitMix64 (Steele, Lea and Flood 2014) keyed by (seed, stream); real entry
  * uses counter i*p + c, complex entry counters 2(i*p + c) and 2(i*p + c) + 1. */

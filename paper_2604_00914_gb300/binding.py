@@ -117,6 +117,7 @@ SIGNATURES = {
     "apf_rayleigh_ritz": (_I32, [_P, _P, _P, _I64, _I64, _P, _P, _I64]),
     "apf_residual_norms": (_I32, [_P, _P, _P, _I64, _I64, _P, _P]),
     "apf_random_block": (_I32, [_P, _I32, _U64, C.c_uint32, _I64, _I64, _P, _I64]),
+    "apf_gram_noalloc": (_I32, [_I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P]),
 }
 
 

@@ -160,6 +160,12 @@ template <class T>
 void gram(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_t ldx,
           const T* Y, int64_t ldy, T* G, int64_t ldg, bool hermitian);
 
+// gram() with the split partials in caller-provided device scratch (no allocation)
+template <class T>
+void gram_scratch(cudaStream_t stream, int num_sms, int64_t n, int64_t pa, int64_t pb, const T* X,
+                  int64_t ldx, const T* Y, int64_t ldy, T* G, int64_t ldg, void* scratch,
+                  size_t scratch_bytes);
+
 // Z (n x pb) = beta Z0 + alpha X M; X: n x pa, M: pa x pb (ldm).  Z may alias Z0.
 // upper: M is upper triangular (rows below the diagonal are skipped).
 template <class T>

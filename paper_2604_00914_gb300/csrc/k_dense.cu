@@ -224,3 +224,43 @@ template void small_gemm<double2>(apf_ctx*, int64_t, int64_t, int64_t, char, con
                                   double, double);
 
 }  // namespace apf
+
+namespace apf {
+
+// G = X^H Y like gram() (full, non-Hermitian tiling), with the split partials
+// in caller-provided device scratch instead of an allocation: the number of
+// row splits is capped so that nsplit * pa * pb elements fit scratch_bytes.
+// Every partial entry that the reduction reads is written first, so the
+// scratch needs no clearing.  Launches on `stream`; throws ApfError.
+template <class T>
+void gram_scratch(cudaStream_t stream, int num_sms, int64_t n, int64_t pa, int64_t pb, const T* X,
+                  int64_t ldx, const T* Y, int64_t ldy, T* G, int64_t ldg, void* scratch,
+                  size_t scratch_bytes) {
+  const size_t per_split = (size_t)pa * pb * sizeof(T);
+  APF_REQUIRE(per_split <= scratch_bytes, APF_ERR_ARG);
+  const int nta = (int)((pa + GT - 1) / GT), ntb = (int)((pb + GT - 1) / GT);
+  const int npairs = nta * ntb;
+  int64_t nsplit = (4LL * num_sms + npairs - 1) / npairs;
+  const int64_t max_split = (n + 255) / 256;
+  if (nsplit > max_split) nsplit = max_split;
+  const int64_t cap = (int64_t)(scratch_bytes / per_split);
+  if (nsplit > cap) nsplit = cap;
+  if (nsplit < 1) nsplit = 1;
+  int64_t rows = (n + nsplit - 1) / nsplit;
+  rows = round_up(rows, GRK);
+  nsplit = (n + rows - 1) / rows;
+  if (nsplit < 1) nsplit = 1;
+  T* part = static_cast<T*>(scratch);
+  dim3 grid((unsigned)npairs, (unsigned)nsplit);
+  k_gram_partial<T><<<grid, 256, 0, stream>>>(n, (int)pa, (int)pb, X, ldx, Y, ldy, ntb, false, rows, part);
+  const int64_t tot = pa * pb;
+  k_gram_reduce<T><<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>((int)pa, (int)pb, (int)nsplit, false,
+                                                                    part, G, ldg);
+  APF_CUDA(cudaGetLastError());
+}
+template void gram_scratch<double>(cudaStream_t, int, int64_t, int64_t, int64_t, const double*, int64_t,
+                                   const double*, int64_t, double*, int64_t, void*, size_t);
+template void gram_scratch<double2>(cudaStream_t, int, int64_t, int64_t, int64_t, const double2*, int64_t,
+                                    const double2*, int64_t, double2*, int64_t, void*, size_t);
+
+}  // namespace apf
