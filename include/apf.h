@@ -94,7 +94,7 @@ typedef struct {
   int32_t lanczos_steps;    /* Lanczos steps for the spectrum bounds (Sec. 3.4), 40 */
   double bound_pad;         /* outward padding of the bounds, fraction of the Ritz spread, 0.01 */
   int32_t filter_precision; /* apf_filter_precision, APF_FILTER_F64 */
-  int32_t spurious_rule;    /* 1: Alg. 4 lines 14-18 on (default); 0: off */
+  int32_t spurious_rule;    /* 1: spurious-eigenvalue test of Alg. 4 (Sec. 3.3.2) on (default); 0: off */
   uint64_t seed;            /* seed of the initial block and Lanczos start vector */
   const void* init_block;   /* optional n x p initial block (row-major, ld = p); NULL: seeded */
   int32_t init_on_device;   /* 1 if init_block is a device pointer */
@@ -185,7 +185,7 @@ apf_status apf_result_destroy(apf_result* r);
 
 /* ---- the steps of the path, callable one by one (device buffers) ---------- */
 
-/* Alg. 4 line 1 (Sec. 2.2, Eq. (c_j), Eq. (m_Lanczos_damping)): the
+/* Set-up of Alg. 4 (Sec. 2.2, Eq. (c_j), Eq. (m_Lanczos_damping)): the
  * coefficients a_j = c_j d_{j,k}, j = 0..k, for the mapped interval
  * [am, bm] inside (-1, 1), to host memory (k + 1 doubles). */
 apf_status apf_filter_coefficients(double am, double bm, int32_t k, int32_t damping,
@@ -225,13 +225,13 @@ apf_status apf_spmm(apf_ctx* ctx, const apf_matrix* A, const void* X, int64_t ld
                     int64_t p, void* Y, int64_t ldy);
 
 /* G = X^H Y: the tall-skinny Gram product of the Cholesky QR and
- * Rayleigh-Ritz steps (Alg. 4 lines 5 and 7).  X: n x pa, Y: n x pb,
+ * Rayleigh-Ritz steps of Alg. 4.  X: n x pa, Y: n x pb,
  * G: pa x pb row-major (ldg >= pb), all device, of `dtype`. */
 apf_status apf_gram(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t pb,
                     const void* X, int64_t ldx, const void* Y, int64_t ldy,
                     void* G, int64_t ldg);
 
-/* Alg. 4 line 5: X (device n x p) is replaced by Q with X = Q R, by CholQR2
+/* Orthogonalisation of Alg. 4: X (device n x p) is replaced by Q with X = Q R, by CholQR2
  * (shifted CholQR3 when the first factorisation breaks down). */
 apf_status apf_cholqr2(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t p, void* X, int64_t ld);
 

@@ -12,13 +12,13 @@ Readings taken where the paper is silent or ambiguous:
   theta_max + |beta_m s_m| + pad (theta_max - theta_min), lambda_min likewise,
   and the two are clipped to the Gershgorin interval, which always holds the
   spectrum.
-* Alg. 4 line 5, orth([V, X]): X is projected against the locked V twice
+* The orthogonalisation of Alg. 4, orth([V, X]): X is projected against the locked V twice
   (block classical Gram-Schmidt), then orthonormalised by Cholesky QR twice
-  (CholQR2).  Q^(i) of line 6 is the new part, orthogonal to V.
+  (CholQR2).  Q^(i) is read as the new part, orthogonal to V.
 * When the first Cholesky factorisation of CholQR2 meets a non-positive pivot,
   the shifted Cholesky QR of Fukaya et al. (SIAM J. Sci. Comput. 2020) with
   shift 11 (n p + p (p + 1)) u ||X||_F^2 runs first (CholQR3).
-* Locking (line 19) uses ||r_j|| <= tau_c ||A|| with ||A|| = max(|lmin|, |lmax|),
+* Locking uses ||r_j|| <= tau_c ||A|| with ||A|| = max(|lmin|, |lmax|),
   the convergence test of Sec. 4.
 * n_check^(i-1) is the value from the last iteration that computed it (0 at
   the start); iterations with e^(i) = 0 leave it and the degree unchanged.
@@ -50,8 +50,8 @@ class Params:
     max_iter: int = 50
     lanczos_steps: int = 40
     bound_pad: float = 0.01
-    spurious_rule: bool = True  # Alg. 4 lines 14-18
-    locking: bool = True        # Alg. 4 lines 19-21 (implicit deflation, Sec. 3.3.3)
+    spurious_rule: bool = True  # spurious-eigenvalue test of Alg. 4 (Sec. 3.3.2)
+    locking: bool = True        # implicit deflation (Sec. 3.3.3)
 
 
 @dataclass
@@ -112,7 +112,7 @@ def lanczos_bounds(A, steps: int, v0: np.ndarray, pad: float = 0.01):
                             res_lo=res_lo, res_hi=res_hi, gersh=(g_lo, g_hi))
 
 
-# --- Alg. 4 line 5: orthogonalisation ------------------------------------------------
+# --- Alg. 4, orthogonalisation ------------------------------------------------
 
 def cholqr(X: np.ndarray):
     """One Cholesky QR: G = X^H X = R^H R, Q = X R^{-1}.  Raises LinAlgError
@@ -169,7 +169,7 @@ def rayleigh_ritz(A, Q: np.ndarray):
 
 
 def residual_norms(A, V: np.ndarray, lam: np.ndarray) -> np.ndarray:
-    """||A v_j - lambda_j v_j||_2 for each column (Alg. 4 line 13)."""
+    """||A v_j - lambda_j v_j||_2 for each column (residual step of Alg. 4)."""
     R = A @ V - V * lam[None, :]
     return np.linalg.norm(R, axis=0)
 
@@ -184,7 +184,7 @@ def tau_s(lam_in: np.ndarray, a: float, b: float) -> float:
 # --- Alg. 4 ----------------------------------------------------------------------------
 
 def setup(A, a: float, b: float, params: Params, v0_lanczos: np.ndarray):
-    """Alg. 4 line 1: l1, l2, ||A||, degrees and the coefficients a_j."""
+    """Set-up of Alg. 4: l1, l2, ||A||, degrees and the coefficients a_j."""
     lmin, lmax, binfo = lanczos_bounds(A, params.lanczos_steps, v0_lanczos, params.bound_pad)
     l1, l2 = cb.linear_map(lmin, lmax)
     normA = max(abs(lmin), abs(lmax))
@@ -206,7 +206,7 @@ def adapolysi(A, a: float, b: float, params: Params, V0: np.ndarray,
     """Alg. 4: FSI with adaptive polynomial filtering.
 
     A: scipy sparse Hermitian (both triangles).  V0: n x p start block (made
-    orthonormal here, line 2).  Returns the locked pairs sorted ascending.
+    orthonormal here).  Returns the locked pairs sorted ascending.
     """
     t0 = time.perf_counter()
     S = setup(A, a, b, params, v0_lanczos)
@@ -222,29 +222,29 @@ def adapolysi(A, a: float, b: float, params: Params, V0: np.ndarray,
     status = "no_convergence"
     spmv_cols = 0
     for it in range(1, params.max_iter + 1):
-        # line 4: filtering with Alg. 2
+        # filtering with Alg. 2
         X = clenshaw_apply(A, coef[:ki + 1], l1, l2, Vhat)
         spmv_cols += ki * X.shape[1]
-        # lines 5-6: orthogonalisation against the locked V, then CholQR2
+        # orthogonalisation against the locked V, then CholQR2
         X = project_out(Vlock, X)
         Q = cholqr2(X)
-        # line 7: Rayleigh-Ritz
+        # Rayleigh-Ritz (Alg. 1)
         lam, Vhat = rayleigh_ritz(A, Q)
         spmv_cols += Q.shape[1]
         res = residual_norms(A, Vhat, lam)
         spmv_cols += Q.shape[1]
-        # line 8: in-interval index set
+        # in-interval index set and count
         I = np.nonzero((lam >= a) & (lam <= b))[0]
         e = I.size
         rec = dict(iter=it, degree=ki, width=Vhat.shape[1], e=e, n_lock=n_lock,
                    max_res_in=float(res[I].max() / normA) if e else None)
-        if e == 0:                       # lines 9-11
+        if e == 0:                       # nothing inside: next iteration
             hist.append(rec)
             continue
-        # line 12: next degree by Alg. 3 (fixed-degree runs keep k)
+        # next degree by Alg. 3 (fixed-degree runs keep k)
         k_next = cb.degree_select(lam, e, coef, l1, l2, params.tau_a) \
             if params.k_fixed == 0 else ki
-        # lines 14-18: spurious-eigenvalue test
+        # spurious-eigenvalue test (Eq. (tau_s), Sec. 3.3.2)
         if params.spurious_rule:
             ts = tau_s(lam[I], a, b)
             Cset = I[res[I] < ts]
@@ -254,7 +254,7 @@ def adapolysi(A, a: float, b: float, params: Params, V0: np.ndarray,
             n_check_prev = n_check
             rec["tau_s"] = ts
             rec["n_check"] = n_check
-        # lines 19-21: lock converged pairs
+        # lock converged pairs (Sec. 3.3.3)
         Lset = I[res[I] <= params.tau_c * normA]
         rec["locked"] = int(Lset.size)
         hist.append(rec)
@@ -268,7 +268,7 @@ def adapolysi(A, a: float, b: float, params: Params, V0: np.ndarray,
             Lam = lam[I]
             Vlock = Vhat[:, I]
         ki = k_next
-        # lines 22-24: stop when every in-interval pair is locked
+        # stop when every in-interval pair is locked
         if done:
             status = "ok"
             break

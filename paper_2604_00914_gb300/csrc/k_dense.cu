@@ -1,5 +1,5 @@
 // Dense FP64 / complex-FP64 products of the orthogonalisation and
-// Rayleigh-Ritz steps (Alg. 4 lines 5-7):
+// Rayleigh-Ritz steps of Alg. 4:
 //   gram       G = X^H Y        (n x pa)^H (n x pb), n >> pa, pb
 //   gemm_tall  Z = b Z0 + a X M (n x pa) (pa x pb)
 //   small_gemm C = a op(A) op(B) + b C   for p x p matrices

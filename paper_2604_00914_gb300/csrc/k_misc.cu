@@ -1,7 +1,7 @@
 // Element-wise and reduction kernels around the filter and the Ritz step:
-// seeded random blocks (SplitMix64), precision casts, residual norms (Alg. 4
-// line 13), the per-column coefficients and recombination of the defect
-// form of the filter, column compaction for locking (Alg. 4 lines 20-21),
+// seeded random blocks (SplitMix64), precision casts, residual norms (the
+// residual step of Alg. 4), the per-column coefficients and recombination of
+// the defect form of the filter, column compaction for locking (Alg. 4),
 // and the vector kernels of the Lanczos bound estimate (Sec. 3.4).
 #include "apf_internal.h"
 

@@ -1,5 +1,5 @@
 // Small dense FP64 factorisations on p x p matrices (p <= APF_MAX_P):
-//  - Cholesky G = R^H R (one CTA, right-looking), for Cholesky QR (Alg. 4 line 5);
+//  - Cholesky G = R^H R (one CTA, right-looking), for Cholesky QR (Alg. 4);
 //  - inverse of an upper triangular R (one warp per column);
 //  - Hermitian eigendecomposition for Rayleigh-Ritz (Alg. 1) and for the
 //    Lanczos tridiagonal matrix: one-sided (Hestenes) Jacobi on M = B + sI,

@@ -368,7 +368,7 @@ struct FilterState {
   }
 };
 
-// ---- Alg. 4 line 5: Cholesky QR ------------------------------------------------------
+// ---- Alg. 4, orthogonalisation: Cholesky QR ------------------------------------------------------
 template <class T>
 static bool cholesky_checked(apf_ctx* ctx, int64_t p, T* G, int64_t ldg, double shift) {
   cholesky_upper<T>(ctx, p, G, ldg, shift);
@@ -442,7 +442,7 @@ static void spmm_plain(apf_ctx* ctx, const apf_matrix* A, const T* X, int64_t ld
                       nullptr, ld, p, nullptr, 0.0, 1.0, Y);
 }
 
-// Alg. 4 lines 5-7 and 13: X (filtered, n x p, destroyed) ->
+// Alg. 4 orthogonalisation, Rayleigh-Ritz and residual steps: X (filtered, n x p, destroyed) ->
 // Vh = Ritz vectors, AVh = A Vh, w = Ritz values (ascending), res = residual norms.
 // CholQR2's second pass is merged with Rayleigh-Ritz:
 //   X1 = X R1^{-1};  G2 = X1^H X1 = R2^H R2;  G3 = X1^H (A X1);
@@ -512,7 +512,7 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
   const int64_t launches0 = ctx->launches;
   apf_stats st{};
 
-  // set-up (Alg. 4 line 1): bounds, map, degrees, coefficients
+  // set-up (Alg. 4): bounds, map, degrees, coefficients
   double bnd[6];
   spectrum_bounds(ctx, A, prm->lanczos_steps, prm->seed, prm->bound_pad, bnd);
   const double lmin = bnd[0], lmax = bnd[1];
@@ -550,7 +550,7 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
   FilterState<T> fs;
   fs.init(ctx, A, ld, l1, l2, coef, prm->filter_precision);
 
-  // Alg. 4 line 2: orthonormal initial block
+  // Alg. 4: orthonormal initial block
   if (prm->init_block) {
     APF_CUDA(cudaMemcpy2DAsync(Vh.p, ld * sizeof(T), prm->init_block, p * sizeof(T), p * sizeof(T), n,
                                prm->init_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -579,7 +579,7 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
     IterEv ev{evp.get(), evp.get(), evp.get(), evp.get(), evp.get(), evp.get()};
     iev.push_back(ev);
     APF_CUDA(cudaEventRecord(ev.e0, ctx->stream));
-    // line 4: filtering (Alg. 2)
+    // filtering (Alg. 2)
     const bool defect = have_ritz && prm->filter_precision == APF_FILTER_F32_DEFECT;
     fs.apply(ki, Vh.as<T>(), defect ? AVh.as<T>() : nullptr, defect ? w : nullptr, pa, X.as<T>(),
              ev.f0, ev.f1, &fc);
@@ -587,7 +587,7 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
     deg_sum += ki;
     ++iters;
     APF_CUDA(cudaEventRecord(ev.e1, ctx->stream));
-    // lines 5-7 and 13: orthogonalisation, Rayleigh-Ritz, residuals
+    // orthogonalisation, Rayleigh-Ritz, residuals
     orth_rr<T>(ctx, A, pa, ld, X.as<T>(), X1.as<T>(), Vlock.as<T>(), nlock, ld, sw, Vh.as<T>(),
                AVh.as<T>(), w, res);
     APF_CUDA(cudaEventRecord(ev.e2, ctx->stream));
@@ -598,7 +598,7 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
     if (derr == DEV_BARRIER_TIMEOUT) throw ApfError{APF_ERR_TIMEOUT, "eigensolver barrier"};
     if (derr != 0) throw ApfError{APF_ERR_CUDA, "device error"};
     have_ritz = true;
-    // line 8: in-interval set
+    // in-interval set and count
     std::vector<int> I;
     for (int c = 0; c < pa; ++c)
       if (hw[(size_t)c] >= prm->a && hw[(size_t)c] <= prm->b) I.push_back(c);
@@ -606,15 +606,15 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
     double maxres = 0.0;
     for (int c : I) maxres = std::max(maxres, hr[(size_t)c] / normA);
     std::vector<double> rec = {(double)ki, (double)pa, (double)e, 0.0, (double)nlock, maxres};
-    if (e == 0) {  // lines 9-11
+    if (e == 0) {  // no Ritz value inside: next iteration
       APF_CUDA(cudaEventRecord(ev.e3, ctx->stream));
       hist.insert(hist.end(), rec.begin(), rec.end());
       continue;
     }
-    // line 12: next degree (Alg. 3)
+    // next degree (Alg. 3)
     const int k_next = prm->k_fixed > 0 ? ki
                                         : degree_select(hw.data(), (int)pa, e, coef.data(), kmax, l1, l2, prm->tau_a);
-    // lines 14-18: spurious Ritz values
+    // spurious Ritz values (Eq. (tau_s), Sec. 3.3.2)
     if (prm->spurious_rule) {
       double tau_s = 1e300;
       for (int c : I) tau_s = std::min(tau_s, std::min(fabs(hw[(size_t)c] - prm->a), fabs(hw[(size_t)c] - prm->b)));
@@ -625,7 +625,7 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
       if (n_check > 0 && n_check == n_check_prev) I = Cs;
       n_check_prev = n_check;
     }
-    // lines 19-21: lock
+    // lock converged pairs (implicit deflation, Sec. 3.3.3)
     std::vector<int> L, keep;
     std::vector<char> inL((size_t)pa, 0);
     for (int c : I)
@@ -662,7 +662,7 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
     }
     APF_CUDA(cudaEventRecord(ev.e3, ctx->stream));
     ki = k_next;
-    if (done) {  // lines 22-24
+    if (done) {  // every in-interval pair locked
       status = APF_OK;
       break;
     }
