@@ -115,6 +115,8 @@ typedef struct {
   double filter_kernel_ms;   /* summed device time of the Clenshaw SpMM launches (CUDA events) */
   double filter_bytes;       /* algorithmic bytes of those launches */
   double max_residual;       /* max ||A v - lambda v|| / ||A|| over the returned pairs */
+  int64_t filter_steps;      /* Clenshaw steps (a two-step launch counts 2) */
+  double filter_step_bytes;  /* algorithmic bytes of the same steps run one per launch */
 } apf_stats;
 
 #define APF_MAX_P 1024

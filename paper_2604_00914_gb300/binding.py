@@ -66,6 +66,7 @@ class apf_stats(C.Structure):
         ("ms_orth", C.c_double), ("ms_rr", C.c_double), ("ms_check", C.c_double),
         ("filter_kernel_ms", C.c_double), ("filter_bytes", C.c_double),
         ("max_residual", C.c_double),
+        ("filter_steps", C.c_int64), ("filter_step_bytes", C.c_double),
     ]
 
     def as_dict(self):

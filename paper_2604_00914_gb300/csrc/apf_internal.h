@@ -69,6 +69,17 @@ struct apf_matrix {
   int64_t* sell_chunk_ptr = nullptr;
   int32_t* sell_col = nullptr;
   int32_t* sell_src = nullptr;
+  int64_t sell_bw = 0;           // max |i - j| (natural row order)
+  // a second SELL-8 copy in reverse Cuthill-McKee row order, for the two-step
+  // filter pass (null when the natural order is already banded)
+  int32_t* perm = nullptr;       // new -> old
+  int32_t* iperm = nullptr;      // old -> new
+  int64_t* psell_chunk_ptr = nullptr;
+  int32_t* psell_col = nullptr;
+  int32_t* psell_src = nullptr;
+  int psell_lmax = 0;
+  int64_t psell_slots = 0;
+  int64_t psell_bw = 0;
   // autotuned Clenshaw-step shape per (element size, vectors per row):
   // value = kind * 10000 + G * 100 + VPT, kind 1 = SELL, 0 = CSR
   std::vector<std::pair<int64_t, int>> tune_cache;
@@ -127,6 +138,17 @@ void clenshaw_step_sell(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* 
                         const typename ScalarTraits<T>::Real* coef_col,
                         typename ScalarTraits<T>::Real coef_scalar,
                         typename ScalarTraits<T>::Real alpha, T* Out);
+// Two consecutive Clenshaw steps in one pass (SELL-8, temporal blocking):
+// bufB = 2 A W - va + f1 Y with W = bufA, then bufA = 2 A bufB - bufA + f2 Y.
+// bandwidth: max |i - j| of the stored pattern; seg_count / pass: see spmm_sell.cuh.
+template <class T, class TA>
+void clenshaw_sell_pair(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* chunk_ptr,
+                        const int32_t* scol, const TA* sval, int lmax, int64_t bandwidth, T* bufA,
+                        T* bufB, const T* va, const T* Y, int64_t ld, int64_t ncols,
+                        const typename ScalarTraits<T>::Real* coef1_col,
+                        typename ScalarTraits<T>::Real coef1,
+                        const typename ScalarTraits<T>::Real* coef2_col,
+                        typename ScalarTraits<T>::Real coef2, unsigned* seg_count, unsigned pass);
 // CSR form with an explicit (G, VPT) shape (0, 0: automatic choice)
 template <class T, class TA>
 void clenshaw_step_shape(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* rowptr,
@@ -212,14 +234,20 @@ void scale_columns(apf_ctx* ctx, int64_t n, int64_t p, const float* f, const T* 
 // Rout = l1 (AV - w V) rounded to FP32 (for the defect filter)
 template <class T>
 void residual_norms(apf_ctx* ctx, int64_t n, int64_t p, const T* AV, const T* V, int64_t ld,
-                    const double* w, double* res, typename LowOf<T>::type* Rout, double l1);
+                    const double* w, double* res, typename LowOf<T>::type* Rout, double l1,
+                    const int32_t* rout_rows = nullptr);  // Rout row i goes to row rout_rows[i]
 // per-column Clenshaw coefficients of the defect recurrence and rho(mu_c)
 void defect_coefficients(apf_ctx* ctx, int64_t p, int64_t ld, int k, const double* coef_dev,
                          const double* lam, double l1, double l2, float* F, double* rho);
 // X = V diag(rho) + hi(D)
 template <class T>
 void defect_combine(apf_ctx* ctx, int64_t n, int64_t p, const T* V, int64_t ldv, const double* rho,
-                    const typename LowOf<T>::type* D, int64_t ldd, T* X, int64_t ldx);
+                    const typename LowOf<T>::type* D, int64_t ldd, T* X, int64_t ldx,
+                    const int32_t* d_rows = nullptr);  // row i of X takes row d_rows[i] of D
+// Y[i, :] = X[src_rows[i], :] converted (src_rows null: plain cast)
+template <class TI, class TO>
+void cast_block_rows(apf_ctx* ctx, int64_t n, int64_t p, const TI* X, int64_t ldx, TO* Y, int64_t ldy,
+                     const int32_t* src_rows);
 // Y[:, j] = X[:, idx[j]], j < m  (idx on device)
 template <class T>
 void gather_columns(apf_ctx* ctx, int64_t n, int64_t m, const int32_t* idx, const T* X, int64_t ldx,

@@ -118,6 +118,77 @@ void apf_params_default(apf_params* p) {
 }  // extern "C"
 
 // ---- matrix ingest ---------------------------------------------------------------
+
+// Reverse Cuthill-McKee ordering (Cuthill and McKee 1969; George 1971):
+// breadth-first search from a pseudo-peripheral vertex of each component,
+// neighbours taken in increasing degree, the visit order reversed.
+// Returns new -> old.
+static std::vector<int32_t> rcm_order(int64_t n, const std::vector<int64_t>& rp,
+                                      const std::vector<int32_t>& ci) {
+  std::vector<int32_t> order;
+  order.reserve((size_t)n);
+  std::vector<char> seen((size_t)n, 0);
+  std::vector<int32_t> level((size_t)n, -1), q((size_t)n), nb;
+  auto deg = [&](int64_t v) { return rp[(size_t)v + 1] - rp[(size_t)v]; };
+  // last level of a BFS from s, restricted to s's component
+  auto bfs_far = [&](int32_t s, int* depth) {
+    std::vector<int32_t> touched;
+    int64_t h = 0, t = 0;
+    q[(size_t)t++] = s;
+    level[(size_t)s] = 0;
+    touched.push_back(s);
+    int32_t best = s;
+    while (h < t) {
+      const int32_t u = q[(size_t)h++];
+      for (int64_t e = rp[(size_t)u]; e < rp[(size_t)u + 1]; ++e) {
+        const int32_t v = ci[(size_t)e];
+        if (level[(size_t)v] < 0) {
+          level[(size_t)v] = level[(size_t)u] + 1;
+          q[(size_t)t++] = v;
+          touched.push_back(v);
+        }
+      }
+    }
+    const int maxl = level[(size_t)q[(size_t)t - 1]];
+    for (int32_t v : touched)
+      if (level[(size_t)v] == maxl && deg(v) < deg(best)) best = v;
+    if (level[(size_t)best] != maxl) best = q[(size_t)t - 1];
+    *depth = maxl;
+    for (int32_t v : touched) level[(size_t)v] = -1;
+    return best;
+  };
+  for (int64_t s0 = 0; s0 < n; ++s0) {
+    if (seen[(size_t)s0]) continue;
+    int32_t start = (int32_t)s0;
+    int depth = -1;
+    for (int it = 0; it < 3; ++it) {
+      int d2 = 0;
+      const int32_t far = bfs_far(start, &d2);
+      if (d2 <= depth) break;
+      depth = d2;
+      start = far;
+    }
+    int64_t h = (int64_t)order.size();
+    order.push_back(start);
+    seen[(size_t)start] = 1;
+    while (h < (int64_t)order.size()) {
+      const int32_t u = order[(size_t)h++];
+      nb.clear();
+      for (int64_t e = rp[(size_t)u]; e < rp[(size_t)u + 1]; ++e) {
+        const int32_t v = ci[(size_t)e];
+        if (!seen[(size_t)v]) {
+          seen[(size_t)v] = 1;
+          nb.push_back(v);
+        }
+      }
+      std::stable_sort(nb.begin(), nb.end(), [&](int32_t x, int32_t y) { return deg(x) < deg(y); });
+      order.insert(order.end(), nb.begin(), nb.end());
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  return order;
+}
+
 template <class V>
 static void ingest_csr(apf_ctx* ctx, int64_t n, const std::vector<int64_t>& rp_in,
                        const std::vector<int32_t>& ci_in, const std::vector<V>& v_in, int dtype,
@@ -175,41 +246,94 @@ static void ingest_csr(apf_ctx* ctx, int64_t n, const std::vector<int64_t>& rp_i
   A->n = n;
   A->nnz = (int64_t)ci.size();
   A->dtype = dtype;
-  // SELL-8 structure (rows in order): used by the FP32 filter when the chunk
-  // padding costs at most half of the stored entries
+  // Row order for the filter: the natural one, or reverse Cuthill-McKee when
+  // that at least halves the bandwidth max |i - j| (a small bandwidth lets the
+  // filter run two steps per pass out of L2).
+  int64_t bw0 = 0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = rp[(size_t)i]; e < rp[(size_t)i + 1]; ++e)
+      bw0 = std::max<int64_t>(bw0, std::abs((int64_t)ci[(size_t)e] - i));
+  std::vector<int32_t> perm, iperm;  // perm: new -> old, iperm: old -> new
+  int64_t bw = bw0;
+  if (bw0 > 4096 && n < INT32_MAX) {
+    perm = rcm_order(n, rp, ci);
+    iperm.assign((size_t)n, 0);
+    for (int64_t r = 0; r < n; ++r) iperm[(size_t)perm[(size_t)r]] = (int32_t)r;
+    int64_t bw1 = 0;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t e = rp[(size_t)i]; e < rp[(size_t)i + 1]; ++e)
+        bw1 = std::max<int64_t>(bw1, std::abs((int64_t)iperm[(size_t)ci[(size_t)e]] - (int64_t)iperm[(size_t)i]));
+    if (2 * bw1 <= bw0) bw = bw1;
+    else { perm.clear(); iperm.clear(); }
+  }
+  const bool permuted = !perm.empty();
+  // SELL-8 structures (chunks of 8 consecutive rows padded to their longest
+  // row), each row's entries in CSR order so that every form sums in the same
+  // order: one in the natural row order, and one in the permuted order when a
+  // permutation was found.  Used when padding costs at most half the entries.
+  struct Sell {
+    std::vector<int64_t> cptr;
+    std::vector<int32_t> col, src;
+    int lmax = 0;
+    int64_t slots = 0;
+  };
   const int CH = 8;
   const int64_t nchunks = (n + CH - 1) / CH;
-  std::vector<int64_t> cptr((size_t)nchunks + 1, 0);
-  int lmax = 0;
-  for (int64_t c = 0; c < nchunks; ++c) {
-    int64_t L = 0;
-    for (int64_t r = c * CH; r < std::min<int64_t>(n, (c + 1) * CH); ++r)
-      L = std::max<int64_t>(L, rp[(size_t)r + 1] - rp[(size_t)r]);
-    lmax = std::max<int>(lmax, (int)L);
-    cptr[(size_t)c + 1] = cptr[(size_t)c] + L * CH;
-  }
-  const int64_t slots = cptr[(size_t)nchunks];
-  const bool sell_ok = slots <= (int64_t)(1.5 * (double)A->nnz) && A->nnz < INT32_MAX && slots < INT32_MAX;
-  std::vector<int32_t> scol, ssrc;
-  if (sell_ok) {
-    scol.assign((size_t)slots, 0);
-    ssrc.assign((size_t)slots, -1);
+  auto build_sell = [&](bool use_perm, Sell& S) {
+    auto old_row = [&](int64_t r) { return use_perm ? (int64_t)perm[(size_t)r] : r; };
+    auto new_col = [&](int32_t c) { return use_perm ? iperm[(size_t)c] : c; };
+    S.cptr.assign((size_t)nchunks + 1, 0);
     for (int64_t c = 0; c < nchunks; ++c) {
-      const int64_t L = (cptr[(size_t)c + 1] - cptr[(size_t)c]) / CH;
+      int64_t L = 0;
+      for (int64_t r = c * CH; r < std::min<int64_t>(n, (c + 1) * CH); ++r) {
+        const int64_t o = old_row(r);
+        L = std::max<int64_t>(L, rp[(size_t)o + 1] - rp[(size_t)o]);
+      }
+      S.lmax = std::max<int>(S.lmax, (int)L);
+      S.cptr[(size_t)c + 1] = S.cptr[(size_t)c] + L * CH;
+    }
+    S.slots = S.cptr[(size_t)nchunks];
+    S.col.assign((size_t)S.slots, 0);
+    S.src.assign((size_t)S.slots, -1);
+    for (int64_t c = 0; c < nchunks; ++c) {
+      const int64_t L = (S.cptr[(size_t)c + 1] - S.cptr[(size_t)c]) / CH;
       for (int64_t r = c * CH; r < (c + 1) * CH; ++r) {
-        const int64_t len = r < n ? rp[(size_t)r + 1] - rp[(size_t)r] : 0;
+        const int64_t o = r < n ? old_row(r) : -1;
+        const int64_t len = o >= 0 ? rp[(size_t)o + 1] - rp[(size_t)o] : 0;
         for (int64_t t = 0; t < L; ++t) {
-          const size_t s = (size_t)(cptr[(size_t)c] + t * CH + (r - c * CH));
+          const size_t sl = (size_t)(S.cptr[(size_t)c] + t * CH + (r - c * CH));
           if (t < len) {
-            scol[s] = ci[(size_t)(rp[(size_t)r] + t)];
-            ssrc[s] = (int32_t)(rp[(size_t)r] + t);
+            S.col[sl] = new_col(ci[(size_t)(rp[(size_t)o] + t)]);
+            S.src[sl] = (int32_t)(rp[(size_t)o] + t);
           } else {
-            scol[s] = (int32_t)(r < n ? r : 0);  // padding: the row itself, value 0
+            S.col[sl] = (int32_t)(r < n ? r : 0);  // padding: the row itself, value 0
           }
         }
       }
     }
+  };
+  int64_t slots0 = 0;
+  {
+    for (int64_t c = 0; c < nchunks; ++c) {
+      int64_t L = 0;
+      for (int64_t r = c * CH; r < std::min<int64_t>(n, (c + 1) * CH); ++r)
+        L = std::max<int64_t>(L, rp[(size_t)r + 1] - rp[(size_t)r]);
+      slots0 += L * CH;
+    }
   }
+  const bool sell_ok = slots0 <= (int64_t)(1.5 * (double)A->nnz) && A->nnz < INT32_MAX && slots0 < INT32_MAX;
+  Sell nat, prm;
+  if (sell_ok) {
+    build_sell(false, nat);
+    if (permuted) {
+      build_sell(true, prm);
+      if (prm.slots > (int64_t)(1.5 * (double)A->nnz) || prm.slots >= INT32_MAX) {
+        perm.clear();
+        iperm.clear();
+      }
+    }
+  }
+  const bool have_perm = sell_ok && !perm.empty();
   try {
     APF_CUDA(cudaMalloc(&A->rowptr, rp.size() * sizeof(int64_t)));
     APF_CUDA(cudaMalloc(&A->colidx, std::max<size_t>(ci.size(), 1) * sizeof(int32_t)));
@@ -219,14 +343,30 @@ static void ingest_csr(apf_ctx* ctx, int64_t n, const std::vector<int64_t>& rp_i
     APF_CUDA(cudaMemcpyAsync(A->vals, vv.data(), vv.size() * sizeof(V), cudaMemcpyHostToDevice, ctx->stream));
     if (sell_ok) {
       A->sell_ok = true;
-      A->sell_lmax = lmax;
-      A->sell_slots = slots;
-      APF_CUDA(cudaMalloc(&A->sell_chunk_ptr, cptr.size() * sizeof(int64_t)));
-      APF_CUDA(cudaMalloc(&A->sell_col, std::max<size_t>(scol.size(), 1) * sizeof(int32_t)));
-      APF_CUDA(cudaMalloc(&A->sell_src, std::max<size_t>(ssrc.size(), 1) * sizeof(int32_t)));
-      APF_CUDA(cudaMemcpyAsync(A->sell_chunk_ptr, cptr.data(), cptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
-      APF_CUDA(cudaMemcpyAsync(A->sell_col, scol.data(), scol.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
-      APF_CUDA(cudaMemcpyAsync(A->sell_src, ssrc.data(), ssrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+      A->sell_lmax = nat.lmax;
+      A->sell_slots = nat.slots;
+      A->sell_bw = bw0;
+      APF_CUDA(cudaMalloc(&A->sell_chunk_ptr, nat.cptr.size() * sizeof(int64_t)));
+      APF_CUDA(cudaMalloc(&A->sell_col, std::max<size_t>(nat.col.size(), 1) * sizeof(int32_t)));
+      APF_CUDA(cudaMalloc(&A->sell_src, std::max<size_t>(nat.src.size(), 1) * sizeof(int32_t)));
+      APF_CUDA(cudaMemcpyAsync(A->sell_chunk_ptr, nat.cptr.data(), nat.cptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+      APF_CUDA(cudaMemcpyAsync(A->sell_col, nat.col.data(), nat.col.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+      APF_CUDA(cudaMemcpyAsync(A->sell_src, nat.src.data(), nat.src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (have_perm) {
+      A->psell_lmax = prm.lmax;
+      A->psell_slots = prm.slots;
+      A->psell_bw = bw;
+      APF_CUDA(cudaMalloc(&A->perm, perm.size() * sizeof(int32_t)));
+      APF_CUDA(cudaMalloc(&A->iperm, iperm.size() * sizeof(int32_t)));
+      APF_CUDA(cudaMemcpyAsync(A->perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+      APF_CUDA(cudaMemcpyAsync(A->iperm, iperm.data(), iperm.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+      APF_CUDA(cudaMalloc(&A->psell_chunk_ptr, prm.cptr.size() * sizeof(int64_t)));
+      APF_CUDA(cudaMalloc(&A->psell_col, std::max<size_t>(prm.col.size(), 1) * sizeof(int32_t)));
+      APF_CUDA(cudaMalloc(&A->psell_src, std::max<size_t>(prm.src.size(), 1) * sizeof(int32_t)));
+      APF_CUDA(cudaMemcpyAsync(A->psell_chunk_ptr, prm.cptr.data(), prm.cptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+      APF_CUDA(cudaMemcpyAsync(A->psell_col, prm.col.data(), prm.col.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+      APF_CUDA(cudaMemcpyAsync(A->psell_src, prm.src.data(), prm.src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
     }
     if (dtype == APF_C128)
       apf::gershgorin<double2>(ctx, n, A->rowptr, A->colidx, static_cast<const double2*>(A->vals), &A->gersh_lo, &A->gersh_hi);
@@ -345,6 +485,11 @@ apf_status apf_matrix_destroy(apf_matrix* A) {
   if (A->sell_chunk_ptr) cudaFree(A->sell_chunk_ptr);
   if (A->sell_col) cudaFree(A->sell_col);
   if (A->sell_src) cudaFree(A->sell_src);
+  if (A->perm) cudaFree(A->perm);
+  if (A->iperm) cudaFree(A->iperm);
+  if (A->psell_chunk_ptr) cudaFree(A->psell_chunk_ptr);
+  if (A->psell_col) cudaFree(A->psell_col);
+  if (A->psell_src) cudaFree(A->psell_src);
   delete A;
   return APF_OK;
 }

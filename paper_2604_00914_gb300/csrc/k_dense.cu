@@ -89,6 +89,9 @@ template <class T>
 void gram(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_t ldx, const T* Y,
           int64_t ldy, T* G, int64_t ldg, bool hermitian) {
   if (pa == 0 || pb == 0) return;
+  // hermitian: only tiles on and above the diagonal are computed; the others
+  // are the conjugate transposes.  Exact for X == Y; for X != Y it is the
+  // upper part of a product known to be Hermitian (X^H A X with A = A^H).
   APF_REQUIRE(!hermitian || pa == pb, APF_ERR_ARG);
   const int nta = (int)((pa + GT - 1) / GT), ntb = (int)((pb + GT - 1) / GT);
   const int npairs = hermitian ? nta * (nta + 1) / 2 : nta * ntb;

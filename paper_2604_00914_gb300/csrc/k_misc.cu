@@ -116,6 +116,32 @@ template void cast_block<double2, float2>(apf_ctx*, int64_t, int64_t, const doub
 template void cast_block<float, double>(apf_ctx*, int64_t, int64_t, const float*, int64_t, double*, int64_t);
 template void cast_block<float2, double2>(apf_ctx*, int64_t, int64_t, const float2*, int64_t, double2*, int64_t);
 
+// Y[i, :] = X[src[i], :] converted (a row gather between orderings)
+template <class TI, class TO>
+__global__ void k_cast_rows(int64_t n, int64_t p, const TI* __restrict__ X, int64_t ldx, TO* __restrict__ Y,
+                            int64_t ldy, const int32_t* __restrict__ src) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * p) return;
+  const int64_t i = e / p, c = e % p;
+  Y[i * ldy + c] = cvt(X[(int64_t)src[i] * ldx + c], (TO*)nullptr);
+}
+
+template <class TI, class TO>
+void cast_block_rows(apf_ctx* ctx, int64_t n, int64_t p, const TI* X, int64_t ldx, TO* Y, int64_t ldy,
+                     const int32_t* src_rows) {
+  if (!src_rows) {
+    cast_block<TI, TO>(ctx, n, p, X, ldx, Y, ldy);
+    return;
+  }
+  if (n * p == 0) return;
+  k_cast_rows<TI, TO><<<grid1d(n * p), 256, 0, ctx->stream>>>(n, p, X, ldx, Y, ldy, src_rows);
+  count_launch(ctx);
+}
+template void cast_block_rows<double, float>(apf_ctx*, int64_t, int64_t, const double*, int64_t, float*, int64_t, const int32_t*);
+template void cast_block_rows<double2, float2>(apf_ctx*, int64_t, int64_t, const double2*, int64_t, float2*, int64_t, const int32_t*);
+template void cast_block_rows<float, double>(apf_ctx*, int64_t, int64_t, const float*, int64_t, double*, int64_t, const int32_t*);
+template void cast_block_rows<float2, double2>(apf_ctx*, int64_t, int64_t, const float2*, int64_t, double2*, int64_t, const int32_t*);
+
 template <class T>
 void copy_block(apf_ctx* ctx, int64_t n, int64_t p, const T* X, int64_t ldx, T* Y, int64_t ldy) {
   if (n * p == 0) return;
@@ -175,7 +201,8 @@ template <class T>
 __global__ void k_residual_partial(int64_t n, int64_t p, const T* __restrict__ AV,
                                    const T* __restrict__ V, int64_t ld, const double* __restrict__ w,
                                    int64_t rows_per_block, double* __restrict__ part,
-                                   typename LowOf<T>::type* Rout, double l1) {
+                                   typename LowOf<T>::type* Rout, double l1,
+                                   const int32_t* __restrict__ rout_rows) {
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_block;
   const int64_t r1 = min(n, r0 + rows_per_block);
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -185,7 +212,7 @@ __global__ void k_residual_partial(int64_t n, int64_t p, const T* __restrict__ A
   for (int64_t i = r0; i < r1; ++i) {
     const T r = sub(AV[i * ld + c], rmul(wc, V[i * ld + c]));
     s += abs2(r);
-    if (Rout) Rout[i * ld + c] = to_lo(rmul(l1, r));
+    if (Rout) Rout[(rout_rows ? (int64_t)rout_rows[i] : i) * ld + c] = to_lo(rmul(l1, r));
   }
   part[(int64_t)blockIdx.y * p + c] = s;
 }
@@ -200,7 +227,8 @@ __global__ void k_colsum_sqrt(int64_t p, int64_t nb, const double* __restrict__ 
 
 template <class T>
 void residual_norms(apf_ctx* ctx, int64_t n, int64_t p, const T* AV, const T* V, int64_t ld,
-                    const double* w, double* res, typename LowOf<T>::type* Rout, double l1) {
+                    const double* w, double* res, typename LowOf<T>::type* Rout, double l1,
+                    const int32_t* rout_rows) {
   if (p == 0) return;
   const int64_t cb = (p + 127) / 128;
   int64_t nb = (4LL * ctx->num_sms + cb - 1) / cb;
@@ -211,14 +239,15 @@ void residual_norms(apf_ctx* ctx, int64_t n, int64_t p, const T* AV, const T* V,
   if (nb < 1) nb = 1;
   DBuf part((size_t)nb * p * sizeof(double), ctx->stream, true);
   dim3 grid((unsigned)cb, (unsigned)nb);
-  k_residual_partial<T><<<grid, 128, 0, ctx->stream>>>(n, p, AV, V, ld, w, rows, part.as<double>(), Rout, l1);
+  k_residual_partial<T><<<grid, 128, 0, ctx->stream>>>(n, p, AV, V, ld, w, rows, part.as<double>(), Rout, l1,
+                                                       rout_rows);
   k_colsum_sqrt<<<grid1d(p, 128), 128, 0, ctx->stream>>>(p, nb, part.as<double>(), res);
   count_launch(ctx, 2);
 }
 template void residual_norms<double>(apf_ctx*, int64_t, int64_t, const double*, const double*, int64_t,
-                                     const double*, double*, float*, double);
+                                     const double*, double*, float*, double, const int32_t*);
 template void residual_norms<double2>(apf_ctx*, int64_t, int64_t, const double2*, const double2*, int64_t,
-                                      const double*, double*, float2*, double);
+                                      const double*, double*, float2*, double, const int32_t*);
 
 // ---- the defect form of the filter -------------------------------------------------------
 // Column c with mu = l1 lam_c + l2 runs the scalar Clenshaw recurrence
@@ -258,26 +287,26 @@ template <class T>
 __global__ void k_defect_combine(int64_t n, int64_t p, const T* __restrict__ V, int64_t ldv,
                                  const double* __restrict__ rho,
                                  const typename LowOf<T>::type* __restrict__ D, int64_t ldd,
-                                 T* __restrict__ X, int64_t ldx) {
+                                 T* __restrict__ X, int64_t ldx, const int32_t* __restrict__ d_rows) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * p) return;
   const int64_t i = e / p, c = e % p;
   T v = rmul(rho[c], V[i * ldv + c]);
-  if (D) v = add(v, to_hi(D[i * ldd + c]));
+  if (D) v = add(v, to_hi(D[(d_rows ? (int64_t)d_rows[i] : i) * ldd + c]));
   X[i * ldx + c] = v;
 }
 
 template <class T>
 void defect_combine(apf_ctx* ctx, int64_t n, int64_t p, const T* V, int64_t ldv, const double* rho,
-                    const typename LowOf<T>::type* D, int64_t ldd, T* X, int64_t ldx) {
+                    const typename LowOf<T>::type* D, int64_t ldd, T* X, int64_t ldx, const int32_t* d_rows) {
   if (n * p == 0) return;
-  k_defect_combine<T><<<grid1d(n * p), 256, 0, ctx->stream>>>(n, p, V, ldv, rho, D, ldd, X, ldx);
+  k_defect_combine<T><<<grid1d(n * p), 256, 0, ctx->stream>>>(n, p, V, ldv, rho, D, ldd, X, ldx, d_rows);
   count_launch(ctx);
 }
 template void defect_combine<double>(apf_ctx*, int64_t, int64_t, const double*, int64_t, const double*,
-                                     const float*, int64_t, double*, int64_t);
+                                     const float*, int64_t, double*, int64_t, const int32_t*);
 template void defect_combine<double2>(apf_ctx*, int64_t, int64_t, const double2*, int64_t, const double*,
-                                      const float2*, int64_t, double2*, int64_t);
+                                      const float2*, int64_t, double2*, int64_t, const int32_t*);
 
 // ---- column gathers and layout changes ----------------------------------------------------
 template <class T>

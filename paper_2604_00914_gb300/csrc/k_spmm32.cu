@@ -36,6 +36,18 @@ void clenshaw_step_sell(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* 
                               coef_col, coef_scalar, alpha, Out);
 }
 
+template <class T, class TA>
+void clenshaw_sell_pair(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* chunk_ptr,
+                        const int32_t* scol, const TA* sval, int lmax, int64_t bandwidth, T* bufA,
+                        T* bufB, const T* va, const T* Y, int64_t ld, int64_t ncols,
+                        const typename ScalarTraits<T>::Real* coef1_col,
+                        typename ScalarTraits<T>::Real coef1,
+                        const typename ScalarTraits<T>::Real* coef2_col,
+                        typename ScalarTraits<T>::Real coef2, unsigned* seg_count, unsigned pass) {
+  clenshaw_sell_pair_launch<T, TA>(ctx, G, VPT, n, chunk_ptr, scol, sval, lmax, bandwidth, bufA, bufB, va, Y,
+                                   ld, ncols, coef1_col, coef1, coef2_col, coef2, seg_count, pass);
+}
+
 template <class TA>
 __global__ void k_sell_gather(int64_t slots, const int32_t* __restrict__ src, const TA* __restrict__ csr,
                               TA* __restrict__ out) {
@@ -62,7 +74,11 @@ void sell_gather_values(apf_ctx* ctx, int64_t slots, const int32_t* src, const T
   template void clenshaw_step_sell<T, T>(apf_ctx*, int, int, int64_t, const int64_t*, const int32_t*, \
                                          const T*, int, const T*, const T*, const T*, int64_t,        \
                                          int64_t, const float*, float, float, T*);                    \
-  template void sell_gather_values<T>(apf_ctx*, int64_t, const int32_t*, const T*, T*);
+  template void sell_gather_values<T>(apf_ctx*, int64_t, const int32_t*, const T*, T*);              \
+  template void clenshaw_sell_pair<T, T>(apf_ctx*, int, int, int64_t, const int64_t*, const int32_t*, \
+                                         const T*, int, int64_t, T*, T*, const T*, const T*, int64_t, \
+                                         int64_t, const float*, float, const float*, float, unsigned*, \
+                                         unsigned);
 APF_INST32(float)
 APF_INST32(float2)
 #undef APF_INST32

@@ -6,6 +6,8 @@
 // library's kernels; the host handles the p Ritz values and index sets of each
 // iteration (one device-to-host transfer of 2 p doubles per iteration).
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <chrono>
@@ -13,7 +15,7 @@
 
 #include "host_math.h"
 #include "solver.h"
-#include "spmm_impl.cuh"
+#include "spmm_sell.cuh"
 
 namespace apf {
 
@@ -100,8 +102,10 @@ void spectrum_bounds(apf_ctx* ctx, const apf_matrix* A, int steps, uint64_t seed
 // ---- Alg. 2: the Clenshaw recurrence over device buffers -------------------------------
 // Counters of the SpMM launches of one filter application.
 struct FilterCount {
-  int64_t launches = 0;
-  double bytes = 0.0;
+  int64_t launches = 0;   // kernel launches
+  int64_t steps = 0;      // Clenshaw steps (a two-step launch counts 2)
+  double bytes = 0.0;     // algorithmic bytes of the launched kernels
+  double step_bytes = 0.0;  // algorithmic bytes of the same steps run one per launch
 };
 
 static double step_bytes(int64_t n, int64_t nnz, int64_t p, size_t sval, size_t sblk, bool vin,
@@ -109,6 +113,14 @@ static double step_bytes(int64_t n, int64_t nnz, int64_t p, size_t sval, size_t 
   const double mat = (double)nnz * (double)(sval + 4) + 8.0 * (double)(n + 1);
   const double streams = 2.0 + (vin ? 1.0 : 0.0) + (y ? 1.0 : 0.0);
   return mat + streams * (double)n * (double)p * (double)sblk;
+}
+
+// two steps in one pass: A once per step, W and V read once, Y read once,
+// both results written (5 block streams; 4 without the first V)
+static double pair_bytes(int64_t n, int64_t nnz, int64_t p, size_t sval, size_t sblk, bool vin) {
+  const double mat = (double)nnz * (double)(sval + 4) + 8.0 * (double)(n + 1);
+  const double streams = 4.0 + (vin ? 1.0 : 0.0);
+  return 2.0 * mat + streams * (double)n * (double)p * (double)sblk;
 }
 
 // One Clenshaw step of the chosen kernel: CSR or SELL-8 storage of A_hat and
@@ -119,12 +131,32 @@ struct Stepper {
   apf_ctx* ctx = nullptr;
   const apf_matrix* A = nullptr;
   const S* csr_vals = nullptr;   // A_hat values in CSR order
-  const S* sell_vals = nullptr;  // A_hat values in SELL-8 order (FP32 only), or null
+  const S* sell_vals = nullptr;   // A_hat values in natural SELL-8 order (FP32 only), or null
+  const S* psell_vals = nullptr;  // A_hat values in permuted SELL-8 order, or null
+  size_t seg_bytes = 0;
   int64_t ld = 0;
-  int kind = 0, G = 0, VPT = 0;  // kind 1: SELL
+  int kind = 0, G = 0, VPT = 0;  // kind 1: SELL, one step per launch; 2: SELL, two steps per launch
+  unsigned* seg_count = nullptr;  // pair-pass counters (kind 2)
+  unsigned* pass = nullptr;       // passes made with seg_count
+  bool pairs() const { return kind == 2; }
+  // bufB = 2 A_hat bufA - va + f1 Y; then bufA = 2 A_hat bufB - bufA + f2 Y
+  void pair(S* bufA, S* bufB, const S* va, const S* Y, int64_t ncols, const Real* f1_col, Real f1,
+            const Real* f2_col, Real f2) const {
+    if constexpr (sizeof(Real) == 4) {
+      *pass += 1;
+      if (A->perm)  // the banded (permuted) copy
+        clenshaw_sell_pair<S, S>(ctx, G, VPT, A->n, A->psell_chunk_ptr, A->psell_col, psell_vals,
+                                 A->psell_lmax, A->psell_bw, bufA, bufB, va, Y, ld, ncols, f1_col, f1, f2_col,
+                                 f2, seg_count, *pass);
+      else
+        clenshaw_sell_pair<S, S>(ctx, G, VPT, A->n, A->sell_chunk_ptr, A->sell_col, sell_vals, A->sell_lmax,
+                                 A->sell_bw, bufA, bufB, va, Y, ld, ncols, f1_col, f1, f2_col, f2, seg_count,
+                                 *pass);
+    }
+  }
   void operator()(const S* W, const S* Vin, const S* Y, int64_t ncols, const Real* coef_col,
                   Real coef_scalar, Real alpha, S* Out) const {
-    if (kind == 1) {
+    if (kind >= 1) {
       if constexpr (sizeof(Real) == 4)
         clenshaw_step_sell<S, S>(ctx, G, VPT, A->n, A->sell_chunk_ptr, A->sell_col, sell_vals,
                                  A->sell_lmax, W, Vin, Y, ld, ncols, coef_col, coef_scalar, alpha, Out);
@@ -164,19 +196,33 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
   std::vector<Cand> cands;
   int g0, v0;
   choose_group(nvec > 256 ? 256 : nvec, &g0, &v0);
-  cands.push_back({0, g0, v0});
+  // SELL shapes run in the SELL row order (possibly permuted), CSR in the
+  // natural one: a matrix with a SELL copy always uses SELL
+  if (!(A->sell_ok && nvec <= 256)) cands.push_back({0, g0, v0});
   if (A->sell_ok && nvec <= 256) {
     static const int shapes[][2] = {{8, 1}, {8, 2}, {8, 3}, {8, 4}, {16, 2}, {16, 3}, {16, 4}, {16, 5},
                                     {16, 6}, {32, 2}, {32, 3}, {32, 4}, {32, 5}, {32, 6}, {32, 8}};
-    for (auto& sh : shapes) {
-      const int g = sh[0], v = sh[1];
+    // shapes with at most 40 % idle vector slots, or the least idle one
+    int least = -1;
+    for (int i = 0; i < (int)(sizeof(shapes) / sizeof(shapes[0])); ++i) {
+      const int gv = shapes[i][0] * shapes[i][1];
+      if (gv >= nvec && (least < 0 || gv < shapes[least][0] * shapes[least][1])) least = i;
+    }
+    for (int i = 0; i < (int)(sizeof(shapes) / sizeof(shapes[0])); ++i) {
+      const int g = shapes[i][0], v = shapes[i][1];
       if (g * v < nvec) continue;
-      if ((double)(g * v - nvec) / (g * v) > 0.4) continue;
+      if ((double)(g * v - nvec) / (g * v) > 0.4 && i != least) continue;
       const int R = 256 / g;
       if ((size_t)R * st.ld * sizeof(S) * 2 + (size_t)R * A->sell_lmax * 12 > 180 * 1024) continue;
       cands.push_back({1, g, v});
+      // two steps per pass when the rows a tile depends on stay within reach of L2
+      const int64_t bwp = A->perm ? A->psell_bw : A->sell_bw;
+      const double window = (double)(2 * bwp + (PAIR_SEG + 1) * R) * st.ld * sizeof(S) * 3.0;
+      if (window <= 64.0 * 1024 * 1024 && (int64_t)R * 4 < A->n) cands.push_back({2, g, v});
     }
   }
+  APF_REQUIRE(!cands.empty(), APF_ERR_ARG);
+  const bool verbose = getenv("APF_VERBOSE") != nullptr;
   cudaEvent_t e0, e1;
   APF_CUDA(cudaEventCreate(&e0));
   APF_CUDA(cudaEventCreate(&e1));
@@ -187,15 +233,29 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
     t.kind = c.kind;
     t.G = c.G;
     t.VPT = c.VPT;
-    t(Wb, Vb, Yb, p, nullptr, (Real)0.5, (Real)2, Ob);
+    // time per Clenshaw step: 4 single steps, or 2 two-step passes
+    auto run = [&]() {
+      if (t.pairs()) {
+        APF_CUDA(cudaMemsetAsync(t.seg_count, 0, st.seg_bytes, st.ctx->stream));
+        *t.pass = 0;
+        t.pair(Ob, const_cast<S*>(Vb), Wb, Yb, p, nullptr, (Real)0.5, nullptr, (Real)0.25);
+        t.pair(Ob, const_cast<S*>(Vb), Vb, Yb, p, nullptr, (Real)0.5, nullptr, (Real)0.25);
+      } else {
+        for (int r = 0; r < 4; ++r) t(Wb, Vb, Yb, p, nullptr, (Real)0.5, (Real)2, Ob);
+      }
+    };
+    run();
     APF_CUDA(cudaEventRecord(e0, st.ctx->stream));
-    for (int r = 0; r < 3; ++r) t(Wb, Vb, Yb, p, nullptr, (Real)0.5, (Real)2, Ob);
+    run();
     APF_CUDA(cudaEventRecord(e1, st.ctx->stream));
     APF_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
     APF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (verbose) fprintf(stderr, "apf tune: nvec %d kind %d G %d VPT %d: %.2f us per step\n", nvec, c.kind,
+                         c.G, c.VPT, 1e3 * ms / 4.0);
     if (ms < best) { best = ms; pick = c; }
   }
+  if (fetch_device_error(st.ctx) != 0) throw ApfError{APF_ERR_TIMEOUT, "filter tuning"};
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   st.kind = pick.kind;
@@ -205,7 +265,8 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
 }
 
 // Plain form: returns the buffer (B1 or B2) that holds rho(A_hat) Y.
-// a: host coefficients a_0..a_k.  ev0/ev1 bracket the SpMM launches.
+// a: host coefficients a_0..a_k.  ev0/ev1 bracket the SpMM launches.  With a
+// two-step stepper the middle steps run in pairs (b_j and b_{j-1} per pass).
 template <class S>
 static S* clenshaw_plain(apf_ctx* ctx, const Stepper<S>& step, int64_t n, int64_t nnz, const S* Y,
                          int64_t ld, int64_t p, const double* a, int k, S* B1, S* B2, cudaEvent_t ev0,
@@ -217,17 +278,35 @@ static S* clenshaw_plain(apf_ctx* ctx, const Stepper<S>& step, int64_t n, int64_
     return B1;
   }
   scale_block<S>(ctx, n, p, a[k], Y, ld, B1, ld);  // b_k = a_k Y
-  S* P1 = B1;
-  S* P2 = nullptr;
+  S* P1 = B1;        // b_{j+1}
+  S* P2 = nullptr;   // b_{j+2} (zero at the start)
   if (ev0) APF_CUDA(cudaEventRecord(ev0, ctx->stream));
-  for (int j = k - 1; j >= 0; --j) {
-    S* out = P2 ? P2 : (P1 == B1 ? B2 : B1);
+  int j = k - 1;
+  while (j >= 0) {
+    S* other = P1 == B1 ? B2 : B1;
+    if (step.pairs() && j >= 2) {
+      // b_j -> other buffer (over b_{j+2}), b_{j-1} -> P1's buffer (over b_{j+1})
+      step.pair(P1, other, P2, Y, p, nullptr, (Real)a[j], nullptr, (Real)a[j - 1]);
+      fc->launches += 1;
+      fc->steps += 2;
+      fc->bytes += pair_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr);
+      fc->step_bytes += step_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr, true) +
+                        step_bytes(n, nnz, p, sizeof(S), sizeof(S), true, true);
+      P2 = other;  // b_j;  P1 now holds b_{j-1}
+      j -= 2;
+      continue;
+    }
+    S* out = P2 ? P2 : other;
     const Real alpha = (j == 0) ? (Real)1 : (Real)2;
     step(P1, P2, Y, p, nullptr, (Real)a[j], alpha, out);
+    const double b = step_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr, true);
     fc->launches += 1;
-    fc->bytes += step_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr, true);
+    fc->steps += 1;
+    fc->bytes += b;
+    fc->step_bytes += b;
     P2 = P1;
     P1 = out;
+    j -= 1;
   }
   if (ev0) APF_CUDA(cudaEventRecord(ev1, ctx->stream));
   return P1;
@@ -252,20 +331,40 @@ static S* clenshaw_defect(apf_ctx* ctx, const Stepper<S>& step, int64_t n, int64
   S* P1 = B1;
   S* P2 = nullptr;  // D_k = 0
   if (ev0) APF_CUDA(cudaEventRecord(ev0, ctx->stream));
-  for (int j = k - 2; j >= 0; --j) {
-    S* out = P2 ? P2 : (P1 == B1 ? B2 : B1);
+  int j = k - 2;
+  while (j >= 0) {
+    S* other = P1 == B1 ? B2 : B1;
+    if (step.pairs() && j >= 2) {
+      step.pair(P1, other, P2, R, p, F + (int64_t)j * ld, 0.0f, F + (int64_t)(j - 1) * ld, 0.0f);
+      fc->launches += 1;
+      fc->steps += 2;
+      fc->bytes += pair_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr);
+      fc->step_bytes += step_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr, true) +
+                        step_bytes(n, nnz, p, sizeof(S), sizeof(S), true, true);
+      P2 = other;
+      j -= 2;
+      continue;
+    }
+    S* out = P2 ? P2 : other;
     const float alpha = (j == 0) ? 1.0f : 2.0f;
     step(P1, P2, R, p, F + (int64_t)j * ld, 0.0f, alpha, out);
+    const double b = step_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr, true);
     fc->launches += 1;
-    fc->bytes += step_bytes(n, nnz, p, sizeof(S), sizeof(S), P2 != nullptr, true);
+    fc->steps += 1;
+    fc->bytes += b;
+    fc->step_bytes += b;
     P2 = P1;
     P1 = out;
+    j -= 1;
   }
   if (ev0) APF_CUDA(cudaEventRecord(ev1, ctx->stream));
   return P1;
 }
 
 // Filter state of one solve: scaled copies of A and the recurrence buffers.
+// With a SELL copy of A the FP32 recurrence runs in the SELL row order (the
+// reverse Cuthill-McKee order when the matrix was permuted): rows are mapped on
+// the way in (perm: new -> old) and on the way out (iperm: old -> new).
 template <class T>
 struct FilterState {
   using TL = typename LowOf<T>::type;
@@ -273,10 +372,12 @@ struct FilterState {
   const apf_matrix* A = nullptr;
   int64_t n = 0, ld = 0;
   double l1 = 0, l2 = 0;
-  DBuf Ahat64, Ahat32, Asell32;  // l1 A + l2 I in FP64 / FP32 (CSR and SELL-8 order)
+  DBuf Ahat64, Ahat32, Asell32, Apsell32;  // l1 A + l2 I: FP64 / FP32 CSR, SELL-8, permuted SELL-8
   DBuf B1, B2, Y32;              // recurrence buffers
   DBuf coef_dev;                 // a_j on the device (defect form)
   DBuf F, rho;                   // defect coefficients
+  DBuf segs;                     // two-step pass counters
+  unsigned pass = 0;
   std::vector<double> a;         // host a_j
   int precision = APF_FILTER_F64;
   int kmax = 0;
@@ -304,6 +405,11 @@ struct FilterState {
       if (A->sell_ok) {
         Asell32.alloc((size_t)A->sell_slots * sizeof(TL), ctx->stream, false);
         sell_gather_values<TL>(ctx, A->sell_slots, A->sell_src, Ahat32.as<TL>(), Asell32.as<TL>());
+        if (A->perm) {
+          Apsell32.alloc((size_t)A->psell_slots * sizeof(TL), ctx->stream, false);
+          sell_gather_values<TL>(ctx, A->psell_slots, A->psell_src, Ahat32.as<TL>(), Apsell32.as<TL>());
+        }
+        segs.alloc(seg_bytes(), ctx->stream, true);
       }
       B1.alloc((size_t)n * ld * sizeof(TL), ctx->stream, true);
       B2.alloc((size_t)n * ld * sizeof(TL), ctx->stream, true);
@@ -316,6 +422,14 @@ struct FilterState {
     }
   }
 
+  // counters for the smallest tile (8 rows): ceil(n / 8 / 32) segments
+  size_t seg_bytes() const { return (size_t)((n + 8 * PAIR_SEG - 1) / (8 * PAIR_SEG) + 1) * sizeof(unsigned); }
+
+  // row maps of the FP32 recurrence: the two-step form of a permuted matrix
+  // runs in the permuted order (null: natural order)
+  const int32_t* rows_in(const Stepper<TL>& st) const { return st.pairs() ? A->perm : nullptr; }
+  const int32_t* rows_out(const Stepper<TL>& st) const { return st.pairs() ? A->iperm : nullptr; }
+
   Stepper<T> stepper64() const {
     Stepper<T> s;
     s.ctx = ctx;
@@ -325,15 +439,23 @@ struct FilterState {
     return s;
   }
 
-  // the tuned FP32 stepper for width p (tuning overwrites B1: call before use)
+  // the tuned FP32 stepper for width p (tuning overwrites B1 and B2: call before use)
   Stepper<TL> stepper32(int64_t p) {
     Stepper<TL> s;
     s.ctx = ctx;
     s.A = A;
     s.csr_vals = Ahat32.as<TL>();
     s.sell_vals = A->sell_ok ? Asell32.as<TL>() : nullptr;
+    s.psell_vals = A->perm ? Apsell32.as<TL>() : nullptr;
     s.ld = ld;
+    s.seg_count = A->sell_ok ? segs.as<unsigned>() : nullptr;
+    s.seg_bytes = A->sell_ok ? seg_bytes() : 0;
+    s.pass = &pass;
     tune_stepper<TL>(s, p, Y32.as<TL>(), B2.as<TL>(), Y32.as<TL>(), B1.as<TL>());
+    if (s.pairs()) {  // fresh counters for this application's passes
+      APF_CUDA(cudaMemsetAsync(segs.p, 0, seg_bytes(), ctx->stream));
+      pass = 0;
+    }
     return s;
   }
 
@@ -352,19 +474,20 @@ struct FilterState {
     }
     const Stepper<TL> st = stepper32(p);
     if (precision == APF_FILTER_F32_DEFECT && AV != nullptr && lam != nullptr) {
-      // R_hat = l1 (A V - V diag(lam)) in FP32; norms are not needed here
+      // R_hat = l1 (A V - V diag(lam)) in FP32, in the recurrence's row order;
+      // the norms are not needed here
       DBuf scratch((size_t)p * sizeof(double), ctx->stream, false);
-      residual_norms<T>(ctx, n, p, AV, V, ld, lam, scratch.as<double>(), Y32.as<TL>(), l1);
+      residual_norms<T>(ctx, n, p, AV, V, ld, lam, scratch.as<double>(), Y32.as<TL>(), l1, rows_out(st));
       defect_coefficients(ctx, p, ld, k, coef_dev.as<double>(), lam, l1, l2, F.as<float>(), rho.as<double>());
       TL* D = clenshaw_defect<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, p, F.as<float>(), k, B1.as<TL>(),
                                   B2.as<TL>(), ev0, ev1, fc);
-      defect_combine<T>(ctx, n, p, V, ld, rho.as<double>(), D, ld, X, ld);
+      defect_combine<T>(ctx, n, p, V, ld, rho.as<double>(), D, ld, X, ld, rows_out(st));
       return;
     }
-    cast_block<T, TL>(ctx, n, p, V, ld, Y32.as<TL>(), ld);
+    cast_block_rows<T, TL>(ctx, n, p, V, ld, Y32.as<TL>(), ld, rows_in(st));
     TL* out = clenshaw_plain<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, p, a.data(), k, B1.as<TL>(),
                                  B2.as<TL>(), ev0, ev1, fc);
-    cast_block<TL, T>(ctx, n, p, out, ld, X, ld);
+    cast_block_rows<TL, T>(ctx, n, p, out, ld, X, ld, rows_out(st));
   }
 };
 
@@ -465,7 +588,7 @@ static void orth_rr(apf_ctx* ctx, const apf_matrix* A, int64_t p, int64_t ld, T*
   T* AX = X;  // X is dead: reuse it for A X1
   spmm_plain<T>(ctx, A, X1, ld, p, AX);
   gram<T>(ctx, n, p, p, X1, ld, X1, ld, sw.G, p, true);
-  gram<T>(ctx, n, p, p, X1, ld, AX, ld, sw.G3, p, false);
+  gram<T>(ctx, n, p, p, X1, ld, AX, ld, sw.G3, p, true);  // X1^H A X1 is Hermitian
   if (!cholesky_checked<T>(ctx, p, sw.G, p, 0.0)) throw ApfError{APF_ERR_CHOL, "CholQR2 second pass"};
   tri_inv_upper<T>(ctx, p, sw.G, p, sw.Ri, p);
   small_gemm<T>(ctx, p, p, p, 'N', sw.G3, p, 'N', sw.Ri, p, sw.T1, p, 1.0, 0.0);
@@ -678,7 +801,9 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
   st.iterations = iters;
   st.avg_degree = iters ? deg_sum / iters : 0.0;
   st.filter_launches = fc.launches;
+  st.filter_steps = fc.steps;
   st.filter_bytes = fc.bytes;
+  st.filter_step_bytes = fc.step_bytes;
 
   // sorted result and its residuals
   const int64_t e = (int64_t)lam_lock.size();

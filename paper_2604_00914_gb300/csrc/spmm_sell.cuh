@@ -64,11 +64,11 @@ __device__ __forceinline__ uint64_t sell_ns() {
   return t;
 }
 
-// Bounded wait for phase 0 of the CTA's barrier.  Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint64_t limit_ns) {
-  if (mbar_try_wait(bar, 0)) return true;
+// Bounded wait for a phase of the CTA's barrier.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = sell_ns();
-  while (!mbar_try_wait(bar, 0)) {
+  while (!mbar_try_wait(bar, parity)) {
     if (sell_ns() - t0 > limit_ns) return false;
   }
   return true;
@@ -85,20 +85,25 @@ inline size_t sell_smem_bytes(int R, int64_t ld, size_t sT, int lmax, size_t sTA
   return b;
 }
 
-template <class T, class TA, int G, int VPT>
-__global__ void __launch_bounds__(256, (VPT <= 4 ? 4 : (VPT <= 6 ? 3 : 2)))
-k_clenshaw_sell(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32_t* __restrict__ scol,
-                const TA* __restrict__ sval, int lmax, const T* __restrict__ W, const T* Vin,
-                const T* __restrict__ Y, int64_t ld, int nvec,
-                const typename ScalarTraits<T>::Real* __restrict__ coef_col,
-                typename ScalarTraits<T>::Real coef_scalar, typename ScalarTraits<T>::Real alpha, T* Out,
-                int* err) {
+struct NoWait {
+  __device__ bool operator()() const { return true; }
+};
+
+// One tile of R = 256 / G rows starting at r0: stage structure, Y and Vin with
+// bulk copies on `bar` (phase `parity`), call wait() (all threads; it may
+// block until other tiles are done), gather W, write Out.  W is read through
+// the non-coherent path unless COHERENT_W (data written earlier in the same
+// launch).  Returns false after a timeout (recorded in err).
+template <class T, class TA, int G, int VPT, bool COHERENT_W, class Wait>
+__device__ __forceinline__ bool sell_tile(
+    int64_t r0, int64_t n, const int64_t* __restrict__ chunk_ptr, const int32_t* __restrict__ scol,
+    const TA* __restrict__ sval, int lmax, const T* W, const T* Vin, const T* Y, int64_t ld, int nvec,
+    const typename ScalarTraits<T>::Real* __restrict__ coef_col, typename ScalarTraits<T>::Real coef_scalar,
+    typename ScalarTraits<T>::Real alpha, T* Out, unsigned char* smem, uint64_t* bar, uint32_t parity,
+    int* err, const Wait& wait) {
   using Real = typename ScalarTraits<T>::Real;
   constexpr int E = ScalarTraits<T>::per16;
   constexpr int R = 256 / G;
-  constexpr int NCH = R / SELL_C;
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   T* Ys = reinterpret_cast<T*>(smem + 128);
   T* Vs = Ys + (Y ? (int64_t)R * ld : 0);
   int32_t* cols = reinterpret_cast<int32_t*>(Vs + (Vin ? (int64_t)R * ld : 0));
@@ -107,14 +112,11 @@ k_clenshaw_sell(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32_t*
   TA* vals = reinterpret_cast<TA*>(smem + voff);
   int64_t* cps = reinterpret_cast<int64_t*>(vals + R * lmax);
 
-  const int64_t r0 = (int64_t)blockIdx.x * R;
   const int nr = (int)((n - r0) < R ? (n - r0) : R);
   const int64_t c0 = r0 / SELL_C;
   const int nch = (nr + SELL_C - 1) / SELL_C;
 
   if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
     uint32_t yv = 0;
     if (Y) yv += (uint32_t)((int64_t)nr * ld * sizeof(T));
     if (Vin) yv += (uint32_t)((int64_t)nr * ld * sizeof(T));
@@ -129,17 +131,17 @@ k_clenshaw_sell(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32_t*
     bulk_g2s(vals, sval + e0, nv, bar);
     mbar_arrive(bar);
   }
-  __syncthreads();
-  if (!mbar_wait_bounded(bar, 1000000000ull)) {
-    atomicCAS(err, 0, DEV_BARRIER_TIMEOUT);
-    mbar_wait_bounded(bar, 1000000000ull);  // let the copies land before leaving
-    return;
+  const bool ready = wait();
+  const bool landed = mbar_wait_bounded(bar, parity, 1000000000ull);
+  if (!__syncthreads_and(ready && landed)) {  // one decision for the whole CTA
+    if (threadIdx.x == 0) atomicCAS(err, 0, DEV_BARRIER_TIMEOUT);
+    mbar_wait_bounded(bar, parity, 1000000000ull);  // let the copies land before leaving
+    return false;
   }
-  (void)NCH;
 
   const int lane = threadIdx.x % G;
   const int rl = threadIdx.x / G;  // local row
-  if (rl >= nr) return;
+  if (rl >= nr) return true;
   const int64_t row = r0 + rl;
   const int cl = rl / SELL_C, rr = rl % SELL_C;
   const int64_t base = cps[cl] - cps[0];
@@ -162,7 +164,8 @@ k_clenshaw_sell(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32_t*
       const int vi = lane + q * G;
       if (vi < nvec) {
         Pack16<T> w;
-        w.u = __ldg(wrow + vi);
+        if constexpr (COHERENT_W) w.u = wrow[vi];  // written earlier in this launch: coherent load
+        else w.u = __ldg(wrow + vi);
 #pragma unroll
         for (int e = 0; e < E; ++e) madd(acc[q][e], v, w.t[e]);
       }
@@ -188,6 +191,149 @@ k_clenshaw_sell(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32_t*
       o.t[e] = r;
     }
     reinterpret_cast<uint4*>(Out + row * ld)[vi] = o.u;
+  }
+  return true;
+}
+
+template <class T, class TA, int G, int VPT>
+__global__ void __launch_bounds__(256, (VPT <= 4 ? 4 : (VPT <= 6 ? 3 : 2)))
+k_clenshaw_sell(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32_t* __restrict__ scol,
+                const TA* __restrict__ sval, int lmax, const T* __restrict__ W, const T* Vin,
+                const T* __restrict__ Y, int64_t ld, int nvec,
+                const typename ScalarTraits<T>::Real* __restrict__ coef_col,
+                typename ScalarTraits<T>::Real coef_scalar, typename ScalarTraits<T>::Real alpha, T* Out,
+                int* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  constexpr int R = 256 / G;
+  sell_tile<T, TA, G, VPT, false>((int64_t)blockIdx.x * R, n, chunk_ptr, scol, sval, lmax, W, Vin, Y, ld,
+                                  nvec, coef_col, coef_scalar, alpha, Out, smem, bar, 0u, err, NoWait());
+}
+
+// ---- two Clenshaw steps in one pass (temporal blocking) -----------------------------
+//
+//   step 1 (tile t):  B[t] = 2 A_hat A_ - Va + f1 .* Y      (b_j from b_{j+1} = A, b_{j+2} = Va)
+//   step 2 (tile t):  A[t] = 2 A_hat B  - A  + f2 .* Y      (b_{j-1} from b_j = B, b_{j+1} = A)
+//
+// A persistent grid walks the work items in a fixed order in which step 2 of
+// tile t comes after step 1 of every tile that it reads (t +- halo tiles) and
+// that reads what it overwrites: step 1 of tile u reads rows of A within the
+// bandwidth of tile u, so once step 1 is done on all tiles within t +- halo,
+// A[t] may be overwritten.  Items are dealt round-robin to the CTAs, each CTA
+// takes its items in order, and a step-2 item waits (bounded in time) until the
+// step-1 counters of the 32-tile segments it depends on reach this pass; every
+// item it waits for sits earlier in the order, so the waits always end.  The
+// rows of B and Y that step 2 reads were touched by step 1 a few hundred tiles
+// earlier and still sit in L2: the pass moves A_, Va and Y in and B and A out
+// (5 block streams) where two single steps move 8.
+constexpr int PAIR_SEG = 32;
+
+struct PairDeps {
+  const unsigned* seg_count;
+  int t, halo, ntiles;
+  unsigned pass;
+  __device__ bool operator()() const {
+    const int lo = (t - halo > 0 ? t - halo : 0) / PAIR_SEG;
+    const int hi = (t + halo < ntiles - 1 ? t + halo : ntiles - 1) / PAIR_SEG;
+    const uint64_t t0 = sell_ns();
+    for (;;) {
+      bool mine = true;
+      for (int s = lo + (int)threadIdx.x; s <= hi; s += (int)blockDim.x) {
+        const int first = s * PAIR_SEG;
+        const int cnt = (ntiles - first) < PAIR_SEG ? (ntiles - first) : PAIR_SEG;
+        const unsigned have = *(volatile const unsigned*)(seg_count + s);
+        if (have < pass * (unsigned)cnt) mine = false;
+      }
+      if (__syncthreads_and(mine)) break;
+      if (__syncthreads_or(sell_ns() - t0 > 1000000000ull)) return false;
+      __nanosleep(128);
+    }
+    __threadfence();
+    return true;
+  }
+};
+
+struct PairArgs {
+  int64_t n;
+  const int64_t* chunk_ptr;
+  const int32_t* scol;
+  const void* sval;
+  int lmax;
+  void* bufA;        // b_{j+1} in, b_{j-1} out
+  void* bufB;        // b_j out (may equal va)
+  const void* va;    // b_{j+2} (nullptr: zero)
+  const void* Y;
+  int64_t ld;
+  int nvec;
+  const void* coef1_col;
+  double coef1;
+  const void* coef2_col;
+  double coef2;
+  int ntiles, halo, lag;
+  unsigned* seg_count;
+  unsigned pass;
+  int* err;
+};
+
+__device__ __forceinline__ void pair_item(int q, int ntiles, int lag, int* kind, int* t) {
+  const int D = lag < ntiles ? lag : ntiles;
+  if (q < D) { *kind = 1; *t = q; return; }
+  const int q2 = q - D, m = ntiles - D;
+  if (q2 < 2 * m) {
+    if ((q2 & 1) == 0) { *kind = 1; *t = D + q2 / 2; }
+    else { *kind = 2; *t = q2 / 2; }
+    return;
+  }
+  *kind = 2;
+  *t = m + (q2 - 2 * m);
+}
+
+template <class T, class TA, int G, int VPT>
+__global__ void __launch_bounds__(256, (VPT <= 4 ? 4 : (VPT <= 6 ? 3 : 2)))
+k_clenshaw_sell_pair(PairArgs a) {
+  using Real = typename ScalarTraits<T>::Real;
+  constexpr int R = 256 / G;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  T* A = static_cast<T*>(a.bufA);
+  T* Bb = static_cast<T*>(a.bufB);
+  const T* Va = static_cast<const T*>(a.va);
+  const T* Y = static_cast<const T*>(a.Y);
+  const TA* sval = static_cast<const TA*>(a.sval);
+  const Real* f1 = static_cast<const Real*>(a.coef1_col);
+  const Real* f2 = static_cast<const Real*>(a.coef2_col);
+  uint32_t parity = 0;
+  const int total = 2 * a.ntiles;
+  for (int q = blockIdx.x; q < total; q += gridDim.x) {
+    int kind, t;
+    pair_item(q, a.ntiles, a.lag, &kind, &t);
+    const int64_t r0 = (int64_t)t * R;
+    bool ok;
+    if (kind == 1) {
+      ok = sell_tile<T, TA, G, VPT, false>(r0, a.n, a.chunk_ptr, a.scol, sval, a.lmax, A, Va, Y, a.ld, a.nvec,
+                                           f1, (Real)a.coef1, (Real)2, Bb, smem, bar, parity, a.err, NoWait());
+    } else {
+      PairDeps deps{a.seg_count, t, a.halo, a.ntiles, a.pass};
+      ok = sell_tile<T, TA, G, VPT, true>(r0, a.n, a.chunk_ptr, a.scol, sval, a.lmax, Bb, A, Y, a.ld, a.nvec,
+                                          f2, (Real)a.coef2, (Real)2, A, smem, bar, parity, a.err, deps);
+    }
+    parity ^= 1u;
+    if (!ok) return;
+    __syncthreads();
+    if (kind == 1 && threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(a.seg_count + t / PAIR_SEG, 1u);
+    }
   }
 }
 
@@ -233,6 +379,75 @@ void clenshaw_sell_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t
   APF_SELL_CASE(32, 2) APF_SELL_CASE(32, 3) APF_SELL_CASE(32, 4) APF_SELL_CASE(32, 5) APF_SELL_CASE(32, 6)
   APF_SELL_CASE(32, 8)
 #undef APF_SELL_CASE
+  APF_REQUIRE(launched, APF_ERR_ARG);
+  count_launch(ctx);
+}
+
+// Two steps in one cooperative launch (every CTA resident, which the ordered
+// waits rely on).  seg_count: ceil(ntiles / 32) counters, zero before the first
+// pass of a buffer set; `pass` counts the passes made with them (from 1).
+template <class T, class TA>
+void clenshaw_sell_pair_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* chunk_ptr,
+                               const int32_t* scol, const TA* sval, int lmax, int64_t bandwidth, T* bufA,
+                               T* bufB, const T* va, const T* Y, int64_t ld, int64_t ncols,
+                               const typename ScalarTraits<T>::Real* coef1_col,
+                               typename ScalarTraits<T>::Real coef1,
+                               const typename ScalarTraits<T>::Real* coef2_col,
+                               typename ScalarTraits<T>::Real coef2, unsigned* seg_count, unsigned pass) {
+  constexpr int E = ScalarTraits<T>::per16;
+  APF_REQUIRE(ld % E == 0 && bufA != bufB && Y != nullptr, APF_ERR_ARG);
+  if (n == 0 || ncols == 0) return;
+  const int nvec = (int)((ncols + E - 1) / E);
+  APF_REQUIRE(nvec <= G * VPT, APF_ERR_ARG);
+  const int R = 256 / G;
+  const size_t smem = sell_smem_bytes(R, ld, sizeof(T), lmax, sizeof(TA), true, true);
+  APF_REQUIRE(smem <= 200 * 1024, APF_ERR_ARG);
+  PairArgs a;
+  a.n = n;
+  a.chunk_ptr = chunk_ptr;
+  a.scol = scol;
+  a.sval = sval;
+  a.lmax = lmax;
+  a.bufA = bufA;
+  a.bufB = bufB;
+  a.va = va;
+  a.Y = Y;
+  a.ld = ld;
+  a.nvec = nvec;
+  a.coef1_col = coef1_col;
+  a.coef1 = (double)coef1;
+  a.coef2_col = coef2_col;
+  a.coef2 = (double)coef2;
+  a.ntiles = (int)((n + R - 1) / R);
+  a.halo = (int)((bandwidth + R - 1) / R);
+  a.seg_count = seg_count;
+  a.pass = pass;
+  a.err = ctx->d_err;
+  bool launched = false;
+#define APF_PAIR_CASE(GG, VV)                                                                         \
+  if (G == GG && VPT == VV) {                                                                         \
+    auto kern = k_clenshaw_sell_pair<T, TA, GG, VV>;                                                  \
+    static bool attr_set = false;                                                                     \
+    if (!attr_set) {                                                                                  \
+      APF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));  \
+      attr_set = true;                                                                                \
+    }                                                                                                 \
+    int per_sm = 0;                                                                                   \
+    APF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));                \
+    APF_REQUIRE(per_sm >= 1, APF_ERR_ARG);                                                            \
+    int grid = per_sm * ctx->num_sms;                                                                 \
+    if (grid > 2 * a.ntiles) grid = 2 * a.ntiles;                                                     \
+    /* step 2 of a tile trails step 1 by the halo, a segment, and half the items in flight */        \
+    a.lag = a.halo + PAIR_SEG + 1 + (grid + 1) / 2;                                                   \
+    void* args[] = {&a};                                                                              \
+    APF_CUDA(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(256), args, smem, ctx->stream)); \
+    launched = true;                                                                                  \
+  }
+  APF_PAIR_CASE(8, 1) APF_PAIR_CASE(8, 2) APF_PAIR_CASE(8, 3) APF_PAIR_CASE(8, 4)
+  APF_PAIR_CASE(16, 2) APF_PAIR_CASE(16, 3) APF_PAIR_CASE(16, 4) APF_PAIR_CASE(16, 5) APF_PAIR_CASE(16, 6)
+  APF_PAIR_CASE(32, 2) APF_PAIR_CASE(32, 3) APF_PAIR_CASE(32, 4) APF_PAIR_CASE(32, 5) APF_PAIR_CASE(32, 6)
+  APF_PAIR_CASE(32, 8)
+#undef APF_PAIR_CASE
   APF_REQUIRE(launched, APF_ERR_ARG);
   count_launch(ctx);
 }
