@@ -169,6 +169,27 @@ void apf_params_default(apf_params* p);
  * locked pairs in ascending order of eigenvalue. */
 apf_status apf_solve(apf_ctx* ctx, const apf_matrix* A, const apf_params* params,
                      apf_result** out);
+/* Spectrum slicing (Sec. 1: the spectrum cut into slices whose eigenpairs are
+ * computed in parallel): Alg. 4 for `nslices` intervals [a[s], b[s]] of the
+ * same matrix with subspace sizes p[s] (host arrays), advanced together.  One
+ * filter launch per Clenshaw step serves every slice: each slice's columns of
+ * the combined block carry that slice's coefficients (zero above its current
+ * degree), so a slice of lower degree simply joins the recurrence later.
+ * Orthogonalisation, Rayleigh-Ritz, locking and Alg. 3 run per slice.
+ * `params` supplies every other setting (its a, b and p are ignored; its
+ * init_block must be NULL: slice s starts from the seeded random block of
+ * stream 1 + s).  The intervals must be pairwise disjoint, 1 <= p[s], and
+ * sum(p) <= min(n, APF_MAX_P); else APF_ERR_ARG.  The result holds the union
+ * of the slices' pairs in ascending order of eigenvalue;
+ * apf_result_slice_counts gives the count per slice (in input order).
+ * APF_ERR_NO_CONVERGENCE if any slice reaches max_iter (partial result). */
+apf_status apf_solve_slices(apf_ctx* ctx, const apf_matrix* A, int32_t nslices, const double* a,
+                            const double* b, const int64_t* p, const apf_params* params,
+                            apf_result** out);
+/* counts[s] = pairs found in slice s (host array of nslices); nslices must be
+ * the number the result was solved with (APF_ERR_ARG otherwise, also for a
+ * result of apf_solve). */
+apf_status apf_result_slice_counts(const apf_result* r, int32_t nslices, int64_t* counts);
 apf_status apf_result_count(const apf_result* r, int64_t* e);
 /* e eigenvalues, ascending, to host memory. */
 apf_status apf_result_eigvals(const apf_result* r, double* host_out);

@@ -99,6 +99,8 @@ SIGNATURES = {
     "apf_matrix_info": (_I32, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I32)]),
     "apf_params_default": (None, [C.POINTER(apf_params)]),
     "apf_solve": (_I32, [_P, _P, C.POINTER(apf_params), C.POINTER(_P)]),
+    "apf_solve_slices": (_I32, [_P, _P, _I32, _P, _P, _P, C.POINTER(apf_params), C.POINTER(_P)]),
+    "apf_result_slice_counts": (_I32, [_P, _I32, _P]),
     "apf_result_count": (_I32, [_P, C.POINTER(_I64)]),
     "apf_result_eigvals": (_I32, [_P, _P]),
     "apf_result_eigvecs": (_I32, [_P, _P, _I64, _I32]),
@@ -306,6 +308,12 @@ class Result:
         self.ctx.lib.check(self.ctx.lib.apf_result_stats(self.h, C.byref(s)))
         return s.as_dict()
 
+    def slice_counts(self, nslices):
+        """Pairs found per slice (apf_solve_slices results only)."""
+        out = np.zeros(int(nslices), dtype=np.int64)
+        self.ctx.lib.check(self.ctx.lib.apf_result_slice_counts(self.h, int(nslices), _ptr(out)))
+        return out
+
     def history(self):
         cnt = C.c_int32()
         self.ctx.lib.check(self.ctx.lib.apf_result_history(self.h, None, 0, C.byref(cnt)))
@@ -329,6 +337,22 @@ def solve(ctx: Context, A: Matrix, params: apf_params, allow_no_convergence=Fals
     """apf_solve.  Raises ApfError on failure (NO_CONVERGENCE too, unless allowed)."""
     h = C.c_void_p()
     st = ctx.lib.apf_solve(ctx.h, A.h, C.byref(params), C.byref(h))
+    if st == APF_ERR_NO_CONVERGENCE and allow_no_convergence:
+        return Result(ctx, h, st)
+    ctx.lib.check(st, ctx.h)
+    return Result(ctx, h, st)
+
+
+def solve_slices(ctx: Context, A: Matrix, a, b, p, params: apf_params, allow_no_convergence=False) -> Result:
+    """apf_solve_slices over the intervals [a[s], b[s]] with subspace sizes p[s]."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.int64)
+    if not (a.shape == b.shape == p.shape and a.ndim == 1):
+        raise ValueError("a, b and p must be 1-d arrays of one length")
+    h = C.c_void_p()
+    st = ctx.lib.apf_solve_slices(ctx.h, A.h, int(a.size), _ptr(a), _ptr(b), _ptr(p), C.byref(params),
+                                  C.byref(h))
     if st == APF_ERR_NO_CONVERGENCE and allow_no_convergence:
         return Result(ctx, h, st)
     ctx.lib.check(st, ctx.h)

@@ -227,9 +227,14 @@ template <class T>
 void copy_block(apf_ctx* ctx, int64_t n, int64_t p, const T* X, int64_t ldx, T* Y, int64_t ldy);
 template <class T>
 void scale_block(apf_ctx* ctx, int64_t n, int64_t p, double s, const T* X, int64_t ldx, T* Y, int64_t ldy);
-// Y[:, c] = f[c] X[:, c] with FP32 coefficients f (device); Y may equal X
+// Y[:, c] = f[c] X[:, c] with coefficients f of X's real type (device); Y may equal X
 template <class T>
-void scale_columns(apf_ctx* ctx, int64_t n, int64_t p, const float* f, const T* X, int64_t ld, T* Y);
+void scale_columns(apf_ctx* ctx, int64_t n, int64_t p, const typename ScalarTraits<T>::Real* f, const T* X,
+                   int64_t ld, T* Y);
+// per-column coefficients of a batched (multi-slice) filter; see k_misc.cu
+template <class TF>
+void coef_columns(apf_ctx* ctx, int64_t p, int64_t ld, int K, const double* coef, const int64_t* coff,
+                  const int32_t* kc, const double* lam, double l1, double l2, TF* F, double* rho);
 // per-column partial sums of |AV - w V|^2 -> res[p] = sqrt (device); optionally
 // Rout = l1 (AV - w V) rounded to FP32 (for the defect filter)
 template <class T>

@@ -526,6 +526,36 @@ apf_status apf_solve(apf_ctx* ctx, const apf_matrix* A, const apf_params* params
   return APF_OK;
 }
 
+apf_status apf_solve_slices(apf_ctx* ctx, const apf_matrix* A, int32_t nslices, const double* a,
+                            const double* b, const int64_t* p, const apf_params* params, apf_result** out) {
+  if (!ctx || !A || !params || !out || A->ctx != ctx || nslices < 1 || !a || !b || !p) return APF_ERR_ARG;
+  apf_result* r = new apf_result();
+  try {
+    bind(ctx);
+    apf::solve_slices(ctx, A, nslices, a, b, p, params, r);
+  } catch (const ApfError& e) {
+    ctx->last_error = e.what;
+    if (e.status == APF_ERR_NO_CONVERGENCE) {
+      *out = r;
+      return e.status;
+    }
+    delete r;
+    cudaStreamSynchronize(ctx->stream);
+    return e.status;
+  } catch (...) {
+    delete r;
+    return APF_ERR_CUDA;
+  }
+  *out = r;
+  return APF_OK;
+}
+
+apf_status apf_result_slice_counts(const apf_result* r, int32_t nslices, int64_t* counts) {
+  if (!r || !counts || nslices < 1 || (size_t)nslices != r->slice_counts.size()) return APF_ERR_ARG;
+  memcpy(counts, r->slice_counts.data(), (size_t)nslices * sizeof(int64_t));
+  return APF_OK;
+}
+
 apf_status apf_result_count(const apf_result* r, int64_t* e) {
   if (!r || !e) return APF_ERR_ARG;
   *e = r->e;

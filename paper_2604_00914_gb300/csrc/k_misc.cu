@@ -177,10 +177,10 @@ template void scale_block<double2>(apf_ctx*, int64_t, int64_t, double, const dou
 template void scale_block<float>(apf_ctx*, int64_t, int64_t, double, const float*, int64_t, float*, int64_t);
 template void scale_block<float2>(apf_ctx*, int64_t, int64_t, double, const float2*, int64_t, float2*, int64_t);
 
-// per-column scaling Y[:, c] = f[c] X[:, c] (f on device, FP32 coefficients)
+// per-column scaling Y[:, c] = f[c] X[:, c] (f on device, coefficients of X's real type)
 template <class T>
-__global__ void k_scale_cols(int64_t n, int64_t p, const float* __restrict__ f, const T* __restrict__ X,
-                             int64_t ld, T* __restrict__ Y) {
+__global__ void k_scale_cols(int64_t n, int64_t p, const typename ScalarTraits<T>::Real* __restrict__ f,
+                             const T* __restrict__ X, int64_t ld, T* __restrict__ Y) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * p) return;
   const int64_t i = e / p, c = e % p;
@@ -188,13 +188,65 @@ __global__ void k_scale_cols(int64_t n, int64_t p, const float* __restrict__ f, 
 }
 
 template <class T>
-void scale_columns(apf_ctx* ctx, int64_t n, int64_t p, const float* f, const T* X, int64_t ld, T* Y) {
+void scale_columns(apf_ctx* ctx, int64_t n, int64_t p, const typename ScalarTraits<T>::Real* f, const T* X,
+                   int64_t ld, T* Y) {
   if (n * p == 0) return;
   k_scale_cols<T><<<grid1d(n * p), 256, 0, ctx->stream>>>(n, p, f, X, ld, Y);
   count_launch(ctx);
 }
 template void scale_columns<float>(apf_ctx*, int64_t, int64_t, const float*, const float*, int64_t, float*);
 template void scale_columns<float2>(apf_ctx*, int64_t, int64_t, const float*, const float2*, int64_t, float2*);
+template void scale_columns<double>(apf_ctx*, int64_t, int64_t, const double*, const double*, int64_t, double*);
+template void scale_columns<double2>(apf_ctx*, int64_t, int64_t, const double*, const double2*, int64_t, double2*);
+
+// Per-column coefficients of a batched filter (spectrum slices): column c uses
+// the coefficient vector coef + coff[c] of degree kc[c], zero above it, inside
+// a recurrence of global degree K.  Plain form (lam == nullptr): F[j][c] = a_j.
+// Defect form: the column's scalar Clenshaw sequence beta_j(mu_c),
+// mu_c = l1 lam_c + l2, gives F[j][c] = 2 beta_{j+1} (0 < j < K), F[0][c] =
+// beta_1 and rho_c = a_0 + mu beta_1 - beta_2.  Padding columns get zeros.
+template <class TF>
+__global__ void k_coef_columns(int64_t p, int64_t ld, int K, const double* __restrict__ coef,
+                               const int64_t* __restrict__ coff, const int32_t* __restrict__ kc,
+                               const double* __restrict__ lam, double l1, double l2, TF* __restrict__ F,
+                               double* __restrict__ rho) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ld) return;
+  if (c >= p) {
+    for (int j = 0; j <= K; ++j) F[(int64_t)j * ld + c] = (TF)0;
+    if (rho) rho[c] = 0.0;
+    return;
+  }
+  const double* a = coef + coff[c];
+  const int k = kc[c];
+  if (!lam) {
+    for (int j = 0; j <= K; ++j) F[(int64_t)j * ld + c] = (TF)(j <= k ? a[j] : 0.0);
+    return;
+  }
+  const double mu = l1 * lam[c] + l2;
+  double b1 = 0.0, b2 = 0.0;  // beta_{j+1}, beta_{j+2}
+  F[(int64_t)K * ld + c] = (TF)0;
+  for (int j = K; j >= 1; --j) {
+    const double aj = j <= k ? a[j] : 0.0;
+    const double bj = aj + 2.0 * mu * b1 - b2;
+    if (j < K) F[(int64_t)j * ld + c] = (TF)(2.0 * b1);
+    b2 = b1;
+    b1 = bj;
+  }
+  F[c] = (TF)b1;
+  rho[c] = a[0] + mu * b1 - b2;
+}
+
+template <class TF>
+void coef_columns(apf_ctx* ctx, int64_t p, int64_t ld, int K, const double* coef, const int64_t* coff,
+                  const int32_t* kc, const double* lam, double l1, double l2, TF* F, double* rho) {
+  k_coef_columns<TF><<<grid1d(ld, 128), 128, 0, ctx->stream>>>(p, ld, K, coef, coff, kc, lam, l1, l2, F, rho);
+  count_launch(ctx);
+}
+template void coef_columns<float>(apf_ctx*, int64_t, int64_t, int, const double*, const int64_t*, const int32_t*,
+                                  const double*, double, double, float*, double*);
+template void coef_columns<double>(apf_ctx*, int64_t, int64_t, int, const double*, const int64_t*, const int32_t*,
+                                   const double*, double, double, double*, double*);
 
 // ---- residual norms ||A v_c - w_c v_c|| (and the mapped residual in FP32) -------------
 template <class T>

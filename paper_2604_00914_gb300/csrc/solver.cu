@@ -361,6 +361,106 @@ static S* clenshaw_defect(apf_ctx* ctx, const Stepper<S>& step, int64_t n, int64
   return P1;
 }
 
+// Batched forms (spectrum slices): per-column coefficient rows F (row j at
+// F + j ld) and the active width of every step: columns are ordered by
+// decreasing degree, so the columns still identically zero at step j (degree
+// below j) are a suffix and are left out.  B1 and B2 must be zero on entry.
+template <class S>
+static S* clenshaw_plain_cols(apf_ctx* ctx, const Stepper<S>& step, int64_t n, int64_t nnz, const S* Y,
+                              int64_t ld, const typename ScalarTraits<S>::Real* F, int K,
+                              const std::vector<int64_t>& act, S* B1, S* B2, cudaEvent_t ev0,
+                              cudaEvent_t ev1, FilterCount* fc) {
+  using Real = typename ScalarTraits<S>::Real;
+  scale_columns<S>(ctx, n, act[(size_t)K], F + (int64_t)K * ld, Y, ld, B1);  // b_K
+  if (K == 0) {
+    if (ev0) { APF_CUDA(cudaEventRecord(ev0, ctx->stream)); APF_CUDA(cudaEventRecord(ev1, ctx->stream)); }
+    return B1;
+  }
+  S* P1 = B1;
+  S* P2 = nullptr;
+  if (ev0) APF_CUDA(cudaEventRecord(ev0, ctx->stream));
+  int j = K - 1;
+  while (j >= 0) {
+    S* other = P1 == B1 ? B2 : B1;
+    if (step.pairs() && j >= 2) {
+      const int64_t w = act[(size_t)(j - 1)];
+      step.pair(P1, other, P2, Y, w, F + (int64_t)j * ld, (Real)0, F + (int64_t)(j - 1) * ld, (Real)0);
+      fc->launches += 1;
+      fc->steps += 2;
+      fc->bytes += pair_bytes(n, nnz, w, sizeof(S), sizeof(S), P2 != nullptr);
+      fc->step_bytes += step_bytes(n, nnz, w, sizeof(S), sizeof(S), P2 != nullptr, true) +
+                        step_bytes(n, nnz, w, sizeof(S), sizeof(S), true, true);
+      P2 = other;
+      j -= 2;
+      continue;
+    }
+    const int64_t w = act[(size_t)j];
+    S* out = P2 ? P2 : other;
+    const Real alpha = (j == 0) ? (Real)1 : (Real)2;
+    step(P1, P2, Y, w, F + (int64_t)j * ld, (Real)0, alpha, out);
+    const double b = step_bytes(n, nnz, w, sizeof(S), sizeof(S), P2 != nullptr, true);
+    fc->launches += 1;
+    fc->steps += 1;
+    fc->bytes += b;
+    fc->step_bytes += b;
+    P2 = P1;
+    P1 = out;
+    j -= 1;
+  }
+  if (ev0) APF_CUDA(cudaEventRecord(ev1, ctx->stream));
+  return P1;
+}
+
+template <class S>
+static S* clenshaw_defect_cols(apf_ctx* ctx, const Stepper<S>& step, int64_t n, int64_t nnz, const S* R,
+                               int64_t ld, const float* F, int K, const std::vector<int64_t>& act, S* B1,
+                               S* B2, cudaEvent_t ev0, cudaEvent_t ev1, FilterCount* fc) {
+  // act[j]: columns with degree > j (D_j can be non-zero only there)
+  if (K == 0) {
+    if (ev0) { APF_CUDA(cudaEventRecord(ev0, ctx->stream)); APF_CUDA(cudaEventRecord(ev1, ctx->stream)); }
+    return nullptr;
+  }
+  if (K == 1) {
+    scale_columns<S>(ctx, n, act[0], F, R, ld, B1);
+    if (ev0) { APF_CUDA(cudaEventRecord(ev0, ctx->stream)); APF_CUDA(cudaEventRecord(ev1, ctx->stream)); }
+    return B1;
+  }
+  scale_columns<S>(ctx, n, act[(size_t)(K - 1)], F + (int64_t)(K - 1) * ld, R, ld, B1);
+  S* P1 = B1;
+  S* P2 = nullptr;
+  if (ev0) APF_CUDA(cudaEventRecord(ev0, ctx->stream));
+  int j = K - 2;
+  while (j >= 0) {
+    S* other = P1 == B1 ? B2 : B1;
+    if (step.pairs() && j >= 2) {
+      const int64_t w = act[(size_t)(j - 1)];
+      step.pair(P1, other, P2, R, w, F + (int64_t)j * ld, 0.0f, F + (int64_t)(j - 1) * ld, 0.0f);
+      fc->launches += 1;
+      fc->steps += 2;
+      fc->bytes += pair_bytes(n, nnz, w, sizeof(S), sizeof(S), P2 != nullptr);
+      fc->step_bytes += step_bytes(n, nnz, w, sizeof(S), sizeof(S), P2 != nullptr, true) +
+                        step_bytes(n, nnz, w, sizeof(S), sizeof(S), true, true);
+      P2 = other;
+      j -= 2;
+      continue;
+    }
+    const int64_t w = act[(size_t)j];
+    S* out = P2 ? P2 : other;
+    const float alpha = (j == 0) ? 1.0f : 2.0f;
+    step(P1, P2, R, w, F + (int64_t)j * ld, 0.0f, alpha, out);
+    const double b = step_bytes(n, nnz, w, sizeof(S), sizeof(S), P2 != nullptr, true);
+    fc->launches += 1;
+    fc->steps += 1;
+    fc->bytes += b;
+    fc->step_bytes += b;
+    P2 = P1;
+    P1 = out;
+    j -= 1;
+  }
+  if (ev0) APF_CUDA(cudaEventRecord(ev1, ctx->stream));
+  return P1;
+}
+
 // Filter state of one solve: scaled copies of A and the recurrence buffers.
 // With a SELL copy of A the FP32 recurrence runs in the SELL row order (the
 // reverse Cuthill-McKee order when the matrix was permuted): rows are mapped on
@@ -414,10 +514,12 @@ struct FilterState {
       B1.alloc((size_t)n * ld * sizeof(TL), ctx->stream, true);
       B2.alloc((size_t)n * ld * sizeof(TL), ctx->stream, true);
       Y32.alloc((size_t)n * ld * sizeof(TL), ctx->stream, true);
-      coef_dev.alloc(coef.size() * sizeof(double), ctx->stream, false);
-      APF_CUDA(cudaMemcpyAsync(coef_dev.p, coef.data(), coef.size() * sizeof(double),
-                               cudaMemcpyHostToDevice, ctx->stream));
-      F.alloc((size_t)(kmax + 1) * ld * sizeof(float), ctx->stream, true);
+      if (!coef.empty()) {  // a batched filter brings its own coefficients
+        coef_dev.alloc(coef.size() * sizeof(double), ctx->stream, false);
+        APF_CUDA(cudaMemcpyAsync(coef_dev.p, coef.data(), coef.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+        F.alloc((size_t)(kmax + 1) * ld * sizeof(float), ctx->stream, true);
+      }
       rho.alloc((size_t)ld * sizeof(double), ctx->stream, true);
     }
   }
@@ -487,6 +589,60 @@ struct FilterState {
     cast_block_rows<T, TL>(ctx, n, p, V, ld, Y32.as<TL>(), ld, rows_in(st));
     TL* out = clenshaw_plain<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, p, a.data(), k, B1.as<TL>(),
                                  B2.as<TL>(), ev0, ev1, fc);
+    cast_block_rows<TL, T>(ctx, n, p, out, ld, X, ld, rows_out(st));
+  }
+
+  // Batched filter (spectrum slices): column c of V (n x p) is filtered with
+  // its own coefficients coef_dev + coff[c] (device) of degree kc[c] (host,
+  // non-increasing in c).  Same forms and precisions as apply().
+  void apply_cols(const std::vector<int32_t>& kc, const std::vector<int64_t>& coff, const double* coef_dev,
+                  const T* V, const T* AV, const double* lam, int64_t p, T* X, cudaEvent_t ev0, cudaEvent_t ev1,
+                  FilterCount* fc) {
+    APF_REQUIRE((int64_t)kc.size() == p && (int64_t)coff.size() == p && p >= 1, APF_ERR_ARG);
+    const int K = kc[0];
+    for (int64_t c = 1; c < p; ++c) APF_REQUIRE(kc[(size_t)c] <= kc[(size_t)c - 1], APF_ERR_ARG);
+    const int64_t nnz = A->nnz;
+    std::vector<int64_t> act_plain((size_t)K + 1, 0), act_def((size_t)K + 1, 0);
+    for (int j = 0; j <= K; ++j) {
+      int64_t wp = 0, wd = 0;
+      while (wp < p && kc[(size_t)wp] >= j) ++wp;
+      while (wd < p && kc[(size_t)wd] > j) ++wd;
+      act_plain[(size_t)j] = wp;
+      act_def[(size_t)j] = wd;
+    }
+    DBuf kcd((size_t)p * sizeof(int32_t), ctx->stream, false), cod((size_t)p * sizeof(int64_t), ctx->stream, false);
+    APF_CUDA(cudaMemcpyAsync(kcd.p, kc.data(), (size_t)p * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    APF_CUDA(cudaMemcpyAsync(cod.p, coff.data(), (size_t)p * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+    if (precision == APF_FILTER_F64) {
+      APF_CUDA(cudaMemsetAsync(B1.p, 0, B1.bytes, ctx->stream));
+      APF_CUDA(cudaMemsetAsync(B2.p, 0, B2.bytes, ctx->stream));
+      DBuf Fd((size_t)(K + 1) * ld * sizeof(double), ctx->stream, false);
+      coef_columns<double>(ctx, p, ld, K, coef_dev, cod.as<int64_t>(), kcd.as<int32_t>(), nullptr, l1, l2,
+                           Fd.as<double>(), nullptr);
+      T* out = clenshaw_plain_cols<T>(ctx, stepper64(), n, nnz, V, ld, Fd.as<double>(), K, act_plain, B1.as<T>(),
+                                      B2.as<T>(), ev0, ev1, fc);
+      copy_block<T>(ctx, n, p, out, ld, X, ld);
+      return;
+    }
+    const Stepper<TL> st = stepper32(p);
+    APF_CUDA(cudaMemsetAsync(B1.p, 0, B1.bytes, ctx->stream));
+    APF_CUDA(cudaMemsetAsync(B2.p, 0, B2.bytes, ctx->stream));
+    DBuf Ff((size_t)(K + 1) * ld * sizeof(float), ctx->stream, false);
+    if (precision == APF_FILTER_F32_DEFECT && AV != nullptr && lam != nullptr) {
+      DBuf scratch((size_t)p * sizeof(double), ctx->stream, false);
+      residual_norms<T>(ctx, n, p, AV, V, ld, lam, scratch.as<double>(), Y32.as<TL>(), l1, rows_out(st));
+      coef_columns<float>(ctx, p, ld, K, coef_dev, cod.as<int64_t>(), kcd.as<int32_t>(), lam, l1, l2,
+                          Ff.as<float>(), rho.as<double>());
+      TL* D = clenshaw_defect_cols<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, Ff.as<float>(), K, act_def,
+                                       B1.as<TL>(), B2.as<TL>(), ev0, ev1, fc);
+      defect_combine<T>(ctx, n, p, V, ld, rho.as<double>(), D, ld, X, ld, rows_out(st));
+      return;
+    }
+    cast_block_rows<T, TL>(ctx, n, p, V, ld, Y32.as<TL>(), ld, rows_in(st));
+    coef_columns<float>(ctx, p, ld, K, coef_dev, cod.as<int64_t>(), kcd.as<int32_t>(), nullptr, l1, l2,
+                        Ff.as<float>(), nullptr);
+    TL* out = clenshaw_plain_cols<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, Ff.as<float>(), K, act_plain,
+                                      B1.as<TL>(), B2.as<TL>(), ev0, ev1, fc);
     cast_block_rows<TL, T>(ctx, n, p, out, ld, X, ld, rows_out(st));
   }
 };
@@ -601,6 +757,190 @@ static void orth_rr(apf_ctx* ctx, const apf_matrix* A, int64_t p, int64_t ld, T*
   residual_norms<T>(ctx, n, p, AVh, Vh, ld, w, res, nullptr, 0.0);
 }
 
+// ---- Alg. 4 for one interval ---------------------------------------------------------------
+// The subspace state of one interval [a, b]: its filter (degrees, coefficients),
+// the active block and the locked pairs.  A single solve runs one; a batched
+// solve runs one per spectrum slice and filters their blocks together.
+template <class T>
+struct IntervalState {
+  double a = 0, b = 0;
+  int64_t p = 0, ld = 0;
+  int k1 = 0, kmax = 0;
+  std::vector<double> coef;  // a_j, j = 0..kmax
+  DBuf Vh, AVh, X, X1, Vlock, wv, resv, idxd;
+  double* w = nullptr;   // Ritz values (device), then a gather scratch at w + ld
+  double* res = nullptr;  // residual norms (device)
+  int64_t pa = 0, nlock = 0;
+  int ki = 0, n_check_prev = 0;
+  bool have_ritz = false;  // Vh holds Ritz vectors with values in w and A Vh in AVh
+  bool done = false;       // every in-interval pair locked
+  std::vector<double> lam_lock, hw, hr;
+  std::vector<double> rec;  // history row of the last iteration
+
+  // set-up (Alg. 4): degrees, coefficients, buffers and the orthonormal initial block
+  void init(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, double a_, double b_, int64_t p_,
+            double l1, double l2, uint32_t stream, SmallWork<T>& sw) {
+    a = a_;
+    b = b_;
+    p = p_;
+    const int64_t n = A->n;
+    APF_REQUIRE(p >= 1 && p <= n && p <= APF_MAX_P, APF_ERR_ARG);
+    APF_REQUIRE(a < b, APF_ERR_ARG);
+    const double am = l1 * a + l2, bm = l1 * b + l2;
+    APF_REQUIRE(am > -1.0 && bm < 1.0 && am < bm, APF_ERR_ARG);
+    if (prm->k_fixed > 0) {
+      k1 = kmax = prm->k_fixed;
+    } else {
+      k1 = initial_degree(am, bm, prm->C);
+      kmax = (int)ceil(prm->k_ratio * k1);
+    }
+    APF_REQUIRE(k1 >= 0 && kmax <= prm->max_degree_cap, APF_ERR_ARG);
+    coef = filter_coefficients(am, bm, kmax, prm->damping, prm->m_d);
+    ld = block_ld(p);
+    const size_t blk = (size_t)n * ld * sizeof(T);
+    Vh.alloc(blk, ctx->stream, true);
+    AVh.alloc(blk, ctx->stream, true);
+    X.alloc(blk, ctx->stream, true);
+    X1.alloc(blk, ctx->stream, true);
+    Vlock.alloc(blk, ctx->stream, true);
+    wv.alloc(sizeof(double) * (size_t)(2 * ld + 8), ctx->stream, true);
+    resv.alloc(sizeof(double) * (size_t)(ld + 8), ctx->stream, true);
+    idxd.alloc(sizeof(int32_t) * (size_t)(2 * ld + 8), ctx->stream, false);
+    w = wv.as<double>();
+    res = resv.as<double>();
+    hw.assign((size_t)p, 0.0);
+    hr.assign((size_t)p, 0.0);
+    pa = p;
+    ki = k1;
+    if (prm->init_block) {
+      APF_CUDA(cudaMemcpy2DAsync(Vh.p, ld * sizeof(T), prm->init_block, p * sizeof(T), p * sizeof(T), n,
+                                 prm->init_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    } else {
+      random_block<T>(ctx, prm->seed, stream, n, p, Vh.as<T>(), ld);
+    }
+    cholqr2_inplace<T>(ctx, n, p, Vh.as<T>(), X1.as<T>(), ld, sw);
+  }
+
+  // after the filter wrote X: orthogonalisation against the locked vectors,
+  // Rayleigh-Ritz and residual norms, and the copies of w and res to the host
+  // (complete after the next synchronisation)
+  void orth(apf_ctx* ctx, const apf_matrix* A, SmallWork<T>& sw) {
+    orth_rr<T>(ctx, A, pa, ld, X.as<T>(), X1.as<T>(), Vlock.as<T>(), nlock, ld, sw, Vh.as<T>(), AVh.as<T>(),
+               w, res);
+    APF_CUDA(cudaMemcpyAsync(hw.data(), w, (size_t)pa * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    APF_CUDA(cudaMemcpyAsync(hr.data(), res, (size_t)pa * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+
+  // on the host values of orth(): in-interval count, next degree (Alg. 3),
+  // spurious-value rule (Eq. (tau_s)), locking and compaction of the block
+  void check(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, double l1, double l2, double normA) {
+    const int64_t n = A->n;
+    have_ritz = true;
+    std::vector<int> I;
+    for (int c = 0; c < pa; ++c)
+      if (hw[(size_t)c] >= a && hw[(size_t)c] <= b) I.push_back(c);
+    const int e = (int)I.size();
+    double maxres = 0.0;
+    for (int c : I) maxres = std::max(maxres, hr[(size_t)c] / normA);
+    rec = {(double)ki, (double)pa, (double)e, 0.0, (double)nlock, maxres};
+    if (e == 0) return;  // no Ritz value inside: same degree again
+    const int k_next =
+        prm->k_fixed > 0 ? ki : degree_select(hw.data(), (int)pa, e, coef.data(), kmax, l1, l2, prm->tau_a);
+    if (prm->spurious_rule) {
+      double tau_s = 1e300;
+      for (int c : I) tau_s = std::min(tau_s, std::min(fabs(hw[(size_t)c] - a), fabs(hw[(size_t)c] - b)));
+      std::vector<int> Cs;
+      for (int c : I)
+        if (hr[(size_t)c] < tau_s) Cs.push_back(c);
+      const int n_check = (int)Cs.size() + (int)nlock;
+      if (n_check > 0 && n_check == n_check_prev) I = Cs;
+      n_check_prev = n_check;
+    }
+    // lock converged pairs (implicit deflation, Sec. 3.3.3)
+    std::vector<int> L, keep;
+    std::vector<char> inL((size_t)pa, 0);
+    for (int c : I)
+      if (hr[(size_t)c] <= prm->tau_c * normA) { L.push_back(c); inL[(size_t)c] = 1; }
+    for (int c = 0; c < pa; ++c)
+      if (!inL[(size_t)c]) keep.push_back(c);
+    rec[3] = (double)L.size();
+    done = L.size() == I.size();
+    if (!L.empty()) {
+      std::vector<int32_t> idx(L.begin(), L.end());
+      idx.insert(idx.end(), keep.begin(), keep.end());
+      APF_CUDA(cudaMemcpyAsync(idxd.p, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+      const int32_t* dL = idxd.as<int32_t>();
+      const int32_t* dK = dL + L.size();
+      gather_columns<T>(ctx, n, (int64_t)L.size(), dL, Vh.as<T>(), ld, Vlock.as<T>() + nlock, ld);
+      for (int c : L) lam_lock.push_back(hw[(size_t)c]);
+      nlock += (int64_t)L.size();
+      const int64_t nk = (int64_t)keep.size();
+      if (nk > 0) {
+        double* w2 = w + ld;
+        gather_columns<T>(ctx, n, nk, dK, Vh.as<T>(), ld, X.as<T>(), ld);
+        copy_block<T>(ctx, n, nk, X.as<T>(), ld, Vh.as<T>(), ld);
+        gather_columns<T>(ctx, n, nk, dK, AVh.as<T>(), ld, X.as<T>(), ld);
+        copy_block<T>(ctx, n, nk, X.as<T>(), ld, AVh.as<T>(), ld);
+        gather_doubles(ctx, nk, dK, w, w2);
+        APF_CUDA(cudaMemcpyAsync(w, w2, (size_t)nk * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+      pa = nk;
+      // the filter buffers' padding columns must stay zero: clear the tail
+      if (pa < ld) {
+        APF_CUDA(cudaMemset2DAsync(Vh.as<T>() + pa, ld * sizeof(T), 0, (size_t)(ld - pa) * sizeof(T), n, ctx->stream));
+        APF_CUDA(cudaMemset2DAsync(AVh.as<T>() + pa, ld * sizeof(T), 0, (size_t)(ld - pa) * sizeof(T), n, ctx->stream));
+      }
+    }
+    ki = k_next;
+  }
+};
+
+// Locked pairs of the intervals (in the given order, each ascending) into the
+// result, with their residuals recomputed from scratch.
+template <class T>
+static void assemble_result(apf_ctx* ctx, const apf_matrix* A, const std::vector<IntervalState<T>*>& ivs,
+                            double normA, apf_result* out) {
+  const int64_t n = A->n;
+  int64_t e = 0;
+  for (auto* s : ivs) e += (int64_t)s->lam_lock.size();
+  out->ctx = ctx;
+  out->n = n;
+  out->e = e;
+  out->dtype = A->dtype;
+  out->lde = block_ld(e);
+  out->lam.clear();
+  out->res.assign((size_t)e, 0.0);
+  out->vecs.alloc((size_t)n * out->lde * sizeof(T), ctx->stream, true);
+  int64_t off = 0;
+  for (auto* s : ivs) {
+    const int64_t es = (int64_t)s->lam_lock.size();
+    std::vector<int32_t> order((size_t)es);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t u, int32_t v) { return s->lam_lock[(size_t)u] < s->lam_lock[(size_t)v]; });
+    for (int64_t j = 0; j < es; ++j) out->lam.push_back(s->lam_lock[(size_t)order[(size_t)j]]);
+    if (es > 0) {
+      DBuf od((size_t)es * sizeof(int32_t), ctx->stream, false);  // freed in stream order
+      APF_CUDA(cudaMemcpyAsync(od.p, order.data(), (size_t)es * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+      gather_columns<T>(ctx, n, es, od.as<int32_t>(), s->Vlock.template as<T>(), s->ld, out->vecs.as<T>() + off, out->lde);
+    }
+    off += es;
+  }
+  if (e > 0) {
+    DBuf lamd((size_t)e * sizeof(double), ctx->stream, false);
+    APF_CUDA(cudaMemcpyAsync(lamd.p, out->lam.data(), (size_t)e * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    DBuf AVr((size_t)n * out->lde * sizeof(T), ctx->stream, true);
+    spmm_plain<T>(ctx, A, out->vecs.as<T>(), out->lde, e, AVr.as<T>());
+    DBuf rd((size_t)e * sizeof(double), ctx->stream, false);
+    residual_norms<T>(ctx, n, e, AVr.as<T>(), out->vecs.as<T>(), out->lde, lamd.as<double>(), rd.as<double>(), nullptr, 0.0);
+    APF_CUDA(cudaMemcpyAsync(out->res.data(), rd.p, (size_t)e * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    APF_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (auto& r : out->res) r /= normA;
+  }
+  APF_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
 // ---- Alg. 4 ---------------------------------------------------------------------------
 static double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
@@ -621,13 +961,54 @@ struct EventPool {
   }
 };
 
+struct IterEv { cudaEvent_t e0, e1, e2, e3, f0, f1; };
+
+static void check_device_after_rr(apf_ctx* ctx) {
+  const int derr = fetch_device_error(ctx);  // synchronises
+  if (derr == DEV_EIGH_NOCONV) throw ApfError{APF_ERR_EIGH, "Rayleigh-Ritz eigensolver"};
+  if (derr == DEV_BARRIER_TIMEOUT) throw ApfError{APF_ERR_TIMEOUT, "eigensolver barrier"};
+  if (derr != 0) throw ApfError{APF_ERR_CUDA, "device error"};
+}
+
+static void finish_stats(apf_ctx* ctx, const std::vector<IterEv>& iev, const FilterCount& fc, int iters,
+                         double deg_sum, apf_stats* st) {
+  APF_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (auto& ev : iev) {
+    st->ms_filter += elapsed_ms(ev.e0, ev.e1);
+    st->ms_rr += elapsed_ms(ev.e1, ev.e2);
+    st->ms_check += elapsed_ms(ev.e2, ev.e3);
+    st->filter_kernel_ms += elapsed_ms(ev.f0, ev.f1);
+  }
+  st->iterations = iters;
+  st->avg_degree = iters ? deg_sum / iters : 0.0;
+  st->filter_launches = fc.launches;
+  st->filter_steps = fc.steps;
+  st->filter_bytes = fc.bytes;
+  st->filter_step_bytes = fc.step_bytes;
+}
+
+struct Bounds {
+  double lmin, lmax, l1, l2, normA;
+};
+
+static Bounds setup_bounds(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm) {
+  double bnd[6];
+  spectrum_bounds(ctx, A, prm->lanczos_steps, prm->seed, prm->bound_pad, bnd);
+  Bounds B;
+  B.lmin = bnd[0];
+  B.lmax = bnd[1];
+  B.l1 = 2.0 / (B.lmax - B.lmin);
+  B.l2 = -(B.lmax + B.lmin) / (B.lmax - B.lmin);
+  B.normA = std::max(fabs(B.lmin), fabs(B.lmax));
+  return B;
+}
+
 template <class T>
 static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, apf_result* out) {
   using clock = std::chrono::steady_clock;
   const auto t_start = clock::now();
   const int64_t n = A->n;
-  const int64_t p = prm->p;
-  APF_REQUIRE(p >= 1 && p <= n && p <= APF_MAX_P, APF_ERR_ARG);
+  APF_REQUIRE(prm->p >= 1 && prm->p <= n && prm->p <= APF_MAX_P, APF_ERR_ARG);
   APF_REQUIRE(prm->a < prm->b, APF_ERR_ARG);
   APF_REQUIRE(prm->max_iter >= 1, APF_ERR_ARG);
   APF_REQUIRE(prm->filter_precision >= APF_FILTER_F64 && prm->filter_precision <= APF_FILTER_F32_DEFECT,
@@ -635,67 +1016,27 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
   const int64_t launches0 = ctx->launches;
   apf_stats st{};
 
-  // set-up (Alg. 4): bounds, map, degrees, coefficients
-  double bnd[6];
-  spectrum_bounds(ctx, A, prm->lanczos_steps, prm->seed, prm->bound_pad, bnd);
-  const double lmin = bnd[0], lmax = bnd[1];
-  const double l1 = 2.0 / (lmax - lmin), l2 = -(lmax + lmin) / (lmax - lmin);
-  const double normA = std::max(fabs(lmin), fabs(lmax));
-  const double am = l1 * prm->a + l2, bm = l1 * prm->b + l2;
-  APF_REQUIRE(am > -1.0 && bm < 1.0 && am < bm, APF_ERR_ARG);
-  int k1, kmax;
-  if (prm->k_fixed > 0) {
-    k1 = kmax = prm->k_fixed;
-  } else {
-    k1 = initial_degree(am, bm, prm->C);
-    kmax = (int)ceil(prm->k_ratio * k1);
-  }
-  APF_REQUIRE(k1 >= 0 && kmax <= prm->max_degree_cap, APF_ERR_ARG);
-  const std::vector<double> coef = filter_coefficients(am, bm, kmax, prm->damping, prm->m_d);
-  st.k1 = k1;
-  st.k_max = kmax;
-  st.lambda_min = lmin;
-  st.lambda_max = lmax;
-  st.norm_a = normA;
-
-  const int64_t ld = block_ld(p);
-  const size_t blk = (size_t)n * ld * sizeof(T);
-  DBuf Vh(blk, ctx->stream, true), AVh(blk, ctx->stream, true), X(blk, ctx->stream, true),
-      X1(blk, ctx->stream, true), Vlock(blk, ctx->stream, true);
-  DBuf wv(sizeof(double) * (size_t)(2 * ld + 8), ctx->stream, true);
-  DBuf resv(sizeof(double) * (size_t)(ld + 8), ctx->stream, true);
-  DBuf idxd(sizeof(int32_t) * (size_t)(2 * ld + 8), ctx->stream, false);
-  double* w = wv.as<double>();
-  double* w2 = w + ld;
-  double* res = resv.as<double>();
+  // set-up (Alg. 4): bounds, map, degrees, coefficients, initial block
+  const Bounds bd = setup_bounds(ctx, A, prm);
   SmallWork<T> sw;
-  sw.init(p, ctx->stream);
+  sw.init(prm->p, ctx->stream);
+  IntervalState<T> S;
+  S.init(ctx, A, prm, prm->a, prm->b, prm->p, bd.l1, bd.l2, 1u, sw);
+  st.k1 = S.k1;
+  st.k_max = S.kmax;
+  st.lambda_min = bd.lmin;
+  st.lambda_max = bd.lmax;
+  st.norm_a = bd.normA;
   FilterState<T> fs;
-  fs.init(ctx, A, ld, l1, l2, coef, prm->filter_precision);
-
-  // Alg. 4: orthonormal initial block
-  if (prm->init_block) {
-    APF_CUDA(cudaMemcpy2DAsync(Vh.p, ld * sizeof(T), prm->init_block, p * sizeof(T), p * sizeof(T), n,
-                               prm->init_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                               ctx->stream));
-  } else {
-    random_block<T>(ctx, prm->seed, 1u, n, p, Vh.as<T>(), ld);
-  }
-  cholqr2_inplace<T>(ctx, n, p, Vh.as<T>(), X1.as<T>(), ld, sw);
+  fs.init(ctx, A, S.ld, bd.l1, bd.l2, S.coef, prm->filter_precision);
   APF_CUDA(cudaStreamSynchronize(ctx->stream));
   st.ms_setup = std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
 
   EventPool evp;
-  struct IterEv { cudaEvent_t e0, e1, e2, e3, f0, f1; };
   std::vector<IterEv> iev;
-  std::vector<double> lam_lock;
   std::vector<double> hist;
-  int64_t pa = p, nlock = 0;
-  int ki = k1, n_check_prev = 0;
-  bool have_ritz = false;  // Vh holds Ritz vectors with values in w and A Vh in AVh
   apf_status status = APF_ERR_NO_CONVERGENCE;
   FilterCount fc;
-  std::vector<double> hw((size_t)p), hr((size_t)p);
   double deg_sum = 0.0;
   int iters = 0;
   for (int it = 1; it <= prm->max_iter; ++it) {
@@ -703,136 +1044,28 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
     iev.push_back(ev);
     APF_CUDA(cudaEventRecord(ev.e0, ctx->stream));
     // filtering (Alg. 2)
-    const bool defect = have_ritz && prm->filter_precision == APF_FILTER_F32_DEFECT;
-    fs.apply(ki, Vh.as<T>(), defect ? AVh.as<T>() : nullptr, defect ? w : nullptr, pa, X.as<T>(),
-             ev.f0, ev.f1, &fc);
-    st.spmv_columns += (int64_t)ki * pa + 2 * pa;
-    deg_sum += ki;
+    const bool defect = S.have_ritz && prm->filter_precision == APF_FILTER_F32_DEFECT;
+    fs.apply(S.ki, S.Vh.template as<T>(), defect ? S.AVh.template as<T>() : nullptr, defect ? S.w : nullptr,
+             S.pa, S.X.template as<T>(), ev.f0, ev.f1, &fc);
+    st.spmv_columns += (int64_t)S.ki * S.pa + 2 * S.pa;
+    deg_sum += S.ki;
     ++iters;
     APF_CUDA(cudaEventRecord(ev.e1, ctx->stream));
     // orthogonalisation, Rayleigh-Ritz, residuals
-    orth_rr<T>(ctx, A, pa, ld, X.as<T>(), X1.as<T>(), Vlock.as<T>(), nlock, ld, sw, Vh.as<T>(),
-               AVh.as<T>(), w, res);
+    S.orth(ctx, A, sw);
     APF_CUDA(cudaEventRecord(ev.e2, ctx->stream));
-    APF_CUDA(cudaMemcpyAsync(hw.data(), w, (size_t)pa * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    APF_CUDA(cudaMemcpyAsync(hr.data(), res, (size_t)pa * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    const int derr = fetch_device_error(ctx);  // synchronises
-    if (derr == DEV_EIGH_NOCONV) throw ApfError{APF_ERR_EIGH, "Rayleigh-Ritz eigensolver"};
-    if (derr == DEV_BARRIER_TIMEOUT) throw ApfError{APF_ERR_TIMEOUT, "eigensolver barrier"};
-    if (derr != 0) throw ApfError{APF_ERR_CUDA, "device error"};
-    have_ritz = true;
-    // in-interval set and count
-    std::vector<int> I;
-    for (int c = 0; c < pa; ++c)
-      if (hw[(size_t)c] >= prm->a && hw[(size_t)c] <= prm->b) I.push_back(c);
-    const int e = (int)I.size();
-    double maxres = 0.0;
-    for (int c : I) maxres = std::max(maxres, hr[(size_t)c] / normA);
-    std::vector<double> rec = {(double)ki, (double)pa, (double)e, 0.0, (double)nlock, maxres};
-    if (e == 0) {  // no Ritz value inside: next iteration
-      APF_CUDA(cudaEventRecord(ev.e3, ctx->stream));
-      hist.insert(hist.end(), rec.begin(), rec.end());
-      continue;
-    }
-    // next degree (Alg. 3)
-    const int k_next = prm->k_fixed > 0 ? ki
-                                        : degree_select(hw.data(), (int)pa, e, coef.data(), kmax, l1, l2, prm->tau_a);
-    // spurious Ritz values (Eq. (tau_s), Sec. 3.3.2)
-    if (prm->spurious_rule) {
-      double tau_s = 1e300;
-      for (int c : I) tau_s = std::min(tau_s, std::min(fabs(hw[(size_t)c] - prm->a), fabs(hw[(size_t)c] - prm->b)));
-      std::vector<int> Cs;
-      for (int c : I)
-        if (hr[(size_t)c] < tau_s) Cs.push_back(c);
-      const int n_check = (int)Cs.size() + (int)nlock;
-      if (n_check > 0 && n_check == n_check_prev) I = Cs;
-      n_check_prev = n_check;
-    }
-    // lock converged pairs (implicit deflation, Sec. 3.3.3)
-    std::vector<int> L, keep;
-    std::vector<char> inL((size_t)pa, 0);
-    for (int c : I)
-      if (hr[(size_t)c] <= prm->tau_c * normA) { L.push_back(c); inL[(size_t)c] = 1; }
-    for (int c = 0; c < pa; ++c)
-      if (!inL[(size_t)c]) keep.push_back(c);
-    rec[3] = (double)L.size();
-    hist.insert(hist.end(), rec.begin(), rec.end());
-    const bool done = L.size() == I.size();
-    if (!L.empty()) {
-      std::vector<int32_t> idx(L.begin(), L.end());
-      idx.insert(idx.end(), keep.begin(), keep.end());
-      APF_CUDA(cudaMemcpyAsync(idxd.p, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
-      const int32_t* dL = idxd.as<int32_t>();
-      const int32_t* dK = dL + L.size();
-      gather_columns<T>(ctx, n, (int64_t)L.size(), dL, Vh.as<T>(), ld, Vlock.as<T>() + nlock, ld);
-      for (int c : L) lam_lock.push_back(hw[(size_t)c]);
-      nlock += (int64_t)L.size();
-      const int64_t nk = (int64_t)keep.size();
-      if (nk > 0) {
-        gather_columns<T>(ctx, n, nk, dK, Vh.as<T>(), ld, X.as<T>(), ld);
-        copy_block<T>(ctx, n, nk, X.as<T>(), ld, Vh.as<T>(), ld);
-        gather_columns<T>(ctx, n, nk, dK, AVh.as<T>(), ld, X.as<T>(), ld);
-        copy_block<T>(ctx, n, nk, X.as<T>(), ld, AVh.as<T>(), ld);
-        gather_doubles(ctx, nk, dK, w, w2);
-        APF_CUDA(cudaMemcpyAsync(w, w2, (size_t)nk * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-      }
-      pa = nk;
-      // the filter buffers' padding columns must stay zero: clear the tail
-      if (pa < ld) {
-        APF_CUDA(cudaMemset2DAsync(Vh.as<T>() + pa, ld * sizeof(T), 0, (size_t)(ld - pa) * sizeof(T), n, ctx->stream));
-        APF_CUDA(cudaMemset2DAsync(AVh.as<T>() + pa, ld * sizeof(T), 0, (size_t)(ld - pa) * sizeof(T), n, ctx->stream));
-      }
-    }
+    check_device_after_rr(ctx);
+    S.check(ctx, A, prm, bd.l1, bd.l2, bd.normA);
     APF_CUDA(cudaEventRecord(ev.e3, ctx->stream));
-    ki = k_next;
-    if (done) {  // every in-interval pair locked
+    hist.insert(hist.end(), S.rec.begin(), S.rec.end());
+    if (S.done) {
       status = APF_OK;
       break;
     }
-    if (pa == 0) break;
+    if (S.pa == 0) break;
   }
-  APF_CUDA(cudaStreamSynchronize(ctx->stream));
-  for (auto& ev : iev) {
-    st.ms_filter += elapsed_ms(ev.e0, ev.e1);
-    st.ms_rr += elapsed_ms(ev.e1, ev.e2);
-    st.ms_check += elapsed_ms(ev.e2, ev.e3);
-    st.filter_kernel_ms += elapsed_ms(ev.f0, ev.f1);
-  }
-  st.iterations = iters;
-  st.avg_degree = iters ? deg_sum / iters : 0.0;
-  st.filter_launches = fc.launches;
-  st.filter_steps = fc.steps;
-  st.filter_bytes = fc.bytes;
-  st.filter_step_bytes = fc.step_bytes;
-
-  // sorted result and its residuals
-  const int64_t e = (int64_t)lam_lock.size();
-  std::vector<int32_t> order((size_t)e);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int32_t u, int32_t v) { return lam_lock[(size_t)u] < lam_lock[(size_t)v]; });
-  out->ctx = ctx;
-  out->n = n;
-  out->e = e;
-  out->dtype = A->dtype;
-  out->lde = block_ld(e);
-  out->lam.resize((size_t)e);
-  out->res.assign((size_t)e, 0.0);
-  for (int64_t j = 0; j < e; ++j) out->lam[(size_t)j] = lam_lock[(size_t)order[(size_t)j]];
-  out->vecs.alloc((size_t)n * out->lde * sizeof(T), ctx->stream, true);
-  if (e > 0) {
-    DBuf od((size_t)e * sizeof(int32_t), ctx->stream, false);
-    DBuf lamd((size_t)e * sizeof(double), ctx->stream, false);
-    APF_CUDA(cudaMemcpyAsync(od.p, order.data(), (size_t)e * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
-    APF_CUDA(cudaMemcpyAsync(lamd.p, out->lam.data(), (size_t)e * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    gather_columns<T>(ctx, n, e, od.as<int32_t>(), Vlock.as<T>(), ld, out->vecs.as<T>(), out->lde);
-    DBuf AVr((size_t)n * out->lde * sizeof(T), ctx->stream, true);
-    spmm_plain<T>(ctx, A, out->vecs.as<T>(), out->lde, e, AVr.as<T>());
-    DBuf rd((size_t)e * sizeof(double), ctx->stream, false);
-    residual_norms<T>(ctx, n, e, AVr.as<T>(), out->vecs.as<T>(), out->lde, lamd.as<double>(), rd.as<double>(), nullptr, 0.0);
-    APF_CUDA(cudaMemcpyAsync(out->res.data(), rd.p, (size_t)e * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    APF_CUDA(cudaStreamSynchronize(ctx->stream));
-    for (auto& r : out->res) r /= normA;
-  }
+  finish_stats(ctx, iev, fc, iters, deg_sum, &st);
+  assemble_result<T>(ctx, A, {&S}, bd.normA, out);
   st.max_residual = 0.0;
   for (double r : out->res) st.max_residual = std::max(st.max_residual, r);
   st.gpu_launches = ctx->launches - launches0;
@@ -842,9 +1075,163 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
   if (status != APF_OK) throw ApfError{status, "no convergence"};
 }
 
+// Spectrum slicing: disjoint intervals [a_s, b_s] with their own subspaces
+// and filters (Sec. 1: the slices are independent problems).  One filter
+// application serves all slices: their blocks are concatenated with the
+// higher degrees first, every column carries its slice's coefficients, and a
+// slice of degree k_s joins the recurrence at step k_s, so all slices finish
+// on the same step.  Orthogonalisation, Rayleigh-Ritz, the spurious rule and
+// locking run per slice, exactly as in a single solve.
+template <class T>
+static void solve_slices_t(apf_ctx* ctx, const apf_matrix* A, int ns, const double* a, const double* b,
+                           const int64_t* p, const apf_params* prm, apf_result* out) {
+  using clock = std::chrono::steady_clock;
+  const auto t_start = clock::now();
+  const int64_t n = A->n;
+  APF_REQUIRE(ns >= 1 && a && b && p, APF_ERR_ARG);
+  APF_REQUIRE(prm->max_iter >= 1 && prm->init_block == nullptr, APF_ERR_ARG);
+  APF_REQUIRE(prm->filter_precision >= APF_FILTER_F64 && prm->filter_precision <= APF_FILTER_F32_DEFECT,
+              APF_ERR_ARG);
+  int64_t ptot = 0, pmax = 0;
+  for (int s = 0; s < ns; ++s) {
+    APF_REQUIRE(p[s] >= 1 && a[s] < b[s], APF_ERR_ARG);
+    ptot += p[s];
+    pmax = std::max(pmax, p[s]);
+  }
+  APF_REQUIRE(ptot <= n && ptot <= APF_MAX_P, APF_ERR_ARG);
+  // slices in ascending order must not overlap
+  std::vector<int> by_a((size_t)ns);
+  std::iota(by_a.begin(), by_a.end(), 0);
+  std::stable_sort(by_a.begin(), by_a.end(), [&](int u, int v) { return a[u] < a[v]; });
+  for (int i = 1; i < ns; ++i) APF_REQUIRE(b[by_a[(size_t)i - 1]] < a[by_a[(size_t)i]], APF_ERR_ARG);
+  const int64_t launches0 = ctx->launches;
+  apf_stats st{};
+
+  const Bounds bd = setup_bounds(ctx, A, prm);
+  SmallWork<T> sw;
+  sw.init(pmax, ctx->stream);
+  std::vector<IntervalState<T>> S((size_t)ns);
+  std::vector<double> coef_all;
+  std::vector<int64_t> coff((size_t)ns);
+  for (int s = 0; s < ns; ++s) {
+    S[(size_t)s].init(ctx, A, prm, a[s], b[s], p[s], bd.l1, bd.l2, 1u + (uint32_t)s, sw);
+    coff[(size_t)s] = (int64_t)coef_all.size();
+    coef_all.insert(coef_all.end(), S[(size_t)s].coef.begin(), S[(size_t)s].coef.end());
+    st.k1 = std::max(st.k1, S[(size_t)s].k1);
+    st.k_max = std::max(st.k_max, S[(size_t)s].kmax);
+  }
+  st.lambda_min = bd.lmin;
+  st.lambda_max = bd.lmax;
+  st.norm_a = bd.normA;
+  DBuf coef_dev(coef_all.size() * sizeof(double), ctx->stream, false);
+  APF_CUDA(cudaMemcpyAsync(coef_dev.p, coef_all.data(), coef_all.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           ctx->stream));
+  // the concatenated blocks
+  const int64_t ldc = block_ld(ptot);
+  const size_t blkc = (size_t)n * ldc * sizeof(T);
+  DBuf Vc(blkc, ctx->stream, true), AVc(blkc, ctx->stream, true), Xc(blkc, ctx->stream, true);
+  DBuf wc(sizeof(double) * (size_t)(ldc + 8), ctx->stream, true);
+  FilterState<T> fs;
+  fs.init(ctx, A, ldc, bd.l1, bd.l2, std::vector<double>(), prm->filter_precision);
+  APF_CUDA(cudaStreamSynchronize(ctx->stream));
+  st.ms_setup = std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
+
+  EventPool evp;
+  std::vector<IterEv> iev;
+  std::vector<double> hist;
+  FilterCount fc;
+  double deg_sum = 0.0;
+  int iters = 0;
+  for (int it = 1; it <= prm->max_iter; ++it) {
+    // active slices, highest degree first
+    std::vector<int> act;
+    for (int s = 0; s < ns; ++s)
+      if (!S[(size_t)s].done && S[(size_t)s].pa > 0) act.push_back(s);
+    if (act.empty()) break;
+    std::stable_sort(act.begin(), act.end(), [&](int u, int v) { return S[(size_t)u].ki > S[(size_t)v].ki; });
+    IterEv ev{evp.get(), evp.get(), evp.get(), evp.get(), evp.get(), evp.get()};
+    iev.push_back(ev);
+    APF_CUDA(cudaEventRecord(ev.e0, ctx->stream));
+    // every active slice has Ritz values or none has (they start together)
+    const bool defect = S[(size_t)act[0]].have_ritz && prm->filter_precision == APF_FILTER_F32_DEFECT;
+    std::vector<int32_t> kc;
+    std::vector<int64_t> co, off;
+    int64_t pc = 0;
+    for (int s : act) {
+      IntervalState<T>& I = S[(size_t)s];
+      off.push_back(pc);
+      copy_block<T>(ctx, n, I.pa, I.Vh.template as<T>(), I.ld, Vc.as<T>() + pc, ldc);
+      if (defect) {
+        copy_block<T>(ctx, n, I.pa, I.AVh.template as<T>(), I.ld, AVc.as<T>() + pc, ldc);
+        APF_CUDA(cudaMemcpyAsync(wc.as<double>() + pc, I.w, (size_t)I.pa * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+      }
+      for (int64_t c = 0; c < I.pa; ++c) {
+        kc.push_back(I.ki);
+        co.push_back(coff[(size_t)s]);
+      }
+      st.spmv_columns += (int64_t)I.ki * I.pa + 2 * I.pa;
+      pc += I.pa;
+    }
+    if (pc < ldc) {  // padding columns of the concatenated blocks stay zero
+      APF_CUDA(cudaMemset2DAsync(Vc.as<T>() + pc, ldc * sizeof(T), 0, (size_t)(ldc - pc) * sizeof(T), n, ctx->stream));
+      if (defect)
+        APF_CUDA(cudaMemset2DAsync(AVc.as<T>() + pc, ldc * sizeof(T), 0, (size_t)(ldc - pc) * sizeof(T), n,
+                                   ctx->stream));
+    }
+    fs.apply_cols(kc, co, coef_dev.as<double>(), Vc.as<T>(), defect ? AVc.as<T>() : nullptr,
+                  defect ? wc.as<double>() : nullptr, pc, Xc.as<T>(), ev.f0, ev.f1, &fc);
+    for (size_t i = 0; i < act.size(); ++i) {
+      IntervalState<T>& I = S[(size_t)act[i]];
+      copy_block<T>(ctx, n, I.pa, Xc.as<T>() + off[i], ldc, I.X.template as<T>(), I.ld);
+    }
+    deg_sum += kc[0];
+    ++iters;
+    APF_CUDA(cudaEventRecord(ev.e1, ctx->stream));
+    for (int s : act) S[(size_t)s].orth(ctx, A, sw);
+    APF_CUDA(cudaEventRecord(ev.e2, ctx->stream));
+    check_device_after_rr(ctx);
+    std::vector<double> row = {(double)kc[0], 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int s : act) {
+      IntervalState<T>& I = S[(size_t)s];
+      I.check(ctx, A, prm, bd.l1, bd.l2, bd.normA);
+      row[1] += I.rec[1];
+      row[2] += I.rec[2];
+      row[3] += I.rec[3];
+      row[4] += I.rec[4];
+      row[5] = std::max(row[5], I.rec[5]);
+    }
+    APF_CUDA(cudaEventRecord(ev.e3, ctx->stream));
+    hist.insert(hist.end(), row.begin(), row.end());
+  }
+  finish_stats(ctx, iev, fc, iters, deg_sum, &st);
+  std::vector<IntervalState<T>*> ordered;
+  for (int s : by_a) ordered.push_back(&S[(size_t)s]);
+  assemble_result<T>(ctx, A, ordered, bd.normA, out);
+  out->slice_counts.assign((size_t)ns, 0);
+  bool all_done = true;
+  for (int s = 0; s < ns; ++s) {
+    out->slice_counts[(size_t)s] = (int64_t)S[(size_t)s].lam_lock.size();
+    all_done = all_done && S[(size_t)s].done;
+  }
+  st.max_residual = 0.0;
+  for (double r : out->res) st.max_residual = std::max(st.max_residual, r);
+  st.gpu_launches = ctx->launches - launches0;
+  st.ms_total = std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
+  out->history = hist;
+  out->stats = st;
+  if (!all_done) throw ApfError{APF_ERR_NO_CONVERGENCE, "no convergence"};
+}
+
 void solve(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, apf_result* out) {
   if (A->dtype == APF_C128) solve_t<double2>(ctx, A, prm, out);
   else solve_t<double>(ctx, A, prm, out);
+}
+
+void solve_slices(apf_ctx* ctx, const apf_matrix* A, int nslices, const double* a, const double* b,
+                  const int64_t* p, const apf_params* prm, apf_result* out) {
+  if (A->dtype == APF_C128) solve_slices_t<double2>(ctx, A, nslices, a, b, p, prm, out);
+  else solve_slices_t<double>(ctx, A, nslices, a, b, p, prm, out);
 }
 
 // ---- the steps one by one, on caller buffers ------------------------------------------

@@ -12,12 +12,15 @@ struct apf_result {
   int64_t lde = 0;
   std::vector<double> lam, res;   // ascending eigenvalues, relative residuals
   std::vector<double> history;    // 6 doubles per iteration
+  std::vector<int64_t> slice_counts;  // per slice, input order (apf_solve_slices)
   apf_stats stats{};
 };
 
 namespace apf {
 
 void solve(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, apf_result* out);
+void solve_slices(apf_ctx* ctx, const apf_matrix* A, int nslices, const double* a, const double* b,
+                  const int64_t* p, const apf_params* prm, apf_result* out);
 
 // Alg. 2 on caller blocks (FP64 input/output of the matrix dtype)
 template <class T>

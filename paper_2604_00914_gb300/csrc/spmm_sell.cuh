@@ -437,8 +437,8 @@ void clenshaw_sell_pair_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const in
     APF_REQUIRE(per_sm >= 1, APF_ERR_ARG);                                                            \
     int grid = per_sm * ctx->num_sms;                                                                 \
     if (grid > 2 * a.ntiles) grid = 2 * a.ntiles;                                                     \
-    /* step 2 of a tile trails step 1 by the halo, a segment, and half the items in flight */        \
-    a.lag = a.halo + PAIR_SEG + 1 + (grid + 1) / 2;                                                   \
+    /* step 2 of a tile trails step 1 by the halo, a segment, and the items in flight */             \
+    a.lag = a.halo + PAIR_SEG + 1 + grid;                                                             \
     void* args[] = {&a};                                                                              \
     APF_CUDA(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(256), args, smem, ctx->stream)); \
     launched = true;                                                                                  \
