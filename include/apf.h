@@ -82,7 +82,7 @@ typedef struct apf_result apf_result;
  * (Sec. 4): m = 0.5, tau_a = 1e-3, C = 1.4, k = ceil(2.5 k^(1)), tau_c = 1e-10. */
 typedef struct {
   double a, b;              /* interval of interest, a < b */
-  int64_t p;                /* subspace size (> 0, <= APF_MAX_P, <= n) */
+  int64_t p;                /* subspace size (<= APF_MAX_P, <= n); 0: estimated, p = ceil(mu e~) (Sec. 3.4) */
   int32_t k_fixed;          /* 0: adaptive degree (Eq. (compute_k_1), Alg. 3); > 0: fixed degree */
   int32_t damping;          /* apf_damping */
   double C;                 /* Eq. (compute_k_1) constant, 1.4 */
@@ -99,6 +99,8 @@ typedef struct {
   const void* init_block;   /* optional n x p initial block (row-major, ld = p); NULL: seeded */
   int32_t init_on_device;   /* 1 if init_block is a device pointer */
   int32_t max_degree_cap;   /* safety cap on the maximum degree k, 100000 */
+  double mu;                /* p = ceil(mu e~) when p = 0 (Sec. 3.4), 1.8 */
+  int32_t trace_probes;     /* probe vectors m of the count estimate e~, 32 */
 } apf_params;
 
 /* Statistics of one solve (the metrics of Table 2 plus per-stage times). */
@@ -117,6 +119,8 @@ typedef struct {
   double max_residual;       /* max ||A v - lambda v|| / ||A|| over the returned pairs */
   int64_t filter_steps;      /* Clenshaw steps (a two-step launch counts 2) */
   double filter_step_bytes;  /* algorithmic bytes of the same steps run one per launch */
+  double trace_estimate;     /* estimated eigenvalue count e~ (sum over slices), 0 if p was given */
+  int64_t p_used;            /* subspace size used (sum over slices) */
 } apf_stats;
 
 #define APF_MAX_P 1024
@@ -242,6 +246,17 @@ apf_status apf_filter_apply_defect(apf_ctx* ctx, const apf_matrix* A, const doub
                                    int32_t degree, double l1, double l2, const void* V,
                                    const void* AV, const double* lam, int64_t ld, int64_t p,
                                    void* Y, int64_t ldy);
+
+/* Sec. 3.4: the eigenvalue count estimate e~ = (1/m) sum_c z_c^H rho(l(A)) z_c,
+ * the trace of the filter rho = sum_{j=0}^{degree} coef[j] T_j (host
+ * coefficients) estimated with m real probe vectors of +-1 (Hutchinson 1989):
+ * z_c[i] = -1 when the uniform draw of counter i m + c of SplitMix64 keyed by
+ * (seed, stream 3) is below 1/2, else +1.  precision: APF_FILTER_F64 or
+ * APF_FILTER_F32 (as apf_filter_apply); 1 <= m <= 8 APF_MAX_P.  *host_out
+ * receives e~.  Allocates (and frees) n x m blocks on the device. */
+apf_status apf_count_estimate(apf_ctx* ctx, const apf_matrix* A, const double* coef,
+                              int32_t degree, double l1, double l2, int32_t precision,
+                              int32_t m, uint64_t seed, double* host_out);
 
 /* Y = A X (FP64 sparse times dense block), device blocks. */
 apf_status apf_spmm(apf_ctx* ctx, const apf_matrix* A, const void* X, int64_t ldx,

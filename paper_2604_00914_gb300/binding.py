@@ -53,6 +53,7 @@ class apf_params(C.Structure):
         ("filter_precision", C.c_int32), ("spurious_rule", C.c_int32),
         ("seed", C.c_uint64), ("init_block", C.c_void_p),
         ("init_on_device", C.c_int32), ("max_degree_cap", C.c_int32),
+        ("mu", C.c_double), ("trace_probes", C.c_int32),
     ]
 
 
@@ -67,6 +68,7 @@ class apf_stats(C.Structure):
         ("filter_kernel_ms", C.c_double), ("filter_bytes", C.c_double),
         ("max_residual", C.c_double),
         ("filter_steps", C.c_int64), ("filter_step_bytes", C.c_double),
+        ("trace_estimate", C.c_double), ("p_used", C.c_int64),
     ]
 
     def as_dict(self):
@@ -111,6 +113,7 @@ SIGNATURES = {
     "apf_filter_coefficients": (_I32, [_D, _D, _I32, _I32, _D, _P]),
     "apf_degree_select": (_I32, [_P, _I32, _I32, _P, _I32, _D, _D, _D, C.POINTER(_I32)]),
     "apf_spectrum_bounds": (_I32, [_P, _P, _I32, _U64, _D, _P]),
+    "apf_count_estimate": (_I32, [_P, _P, _P, _I32, _D, _D, _I32, _I32, _U64, _DP]),
     "apf_filter_apply": (_I32, [_P, _P, _P, _I32, _D, _D, _I32, _P, _I64, _I64, _P, _I64]),
     "apf_filter_apply_defect": (_I32, [_P, _P, _P, _I32, _D, _D, _P, _P, _P, _I64, _I64, _P, _I64]),
     "apf_spmm": (_I32, [_P, _P, _P, _I64, _I64, _P, _I64]),
@@ -382,6 +385,15 @@ def spectrum_bounds(ctx, A, steps=40, seed=20260401, pad=0.01):
     out = np.zeros(6)
     ctx.lib.check(ctx.lib.apf_spectrum_bounds(ctx.h, A.h, int(steps), int(seed), float(pad), _ptr(out)), ctx.h)
     return out
+
+
+def count_estimate(ctx, A, coef, l1, l2, m, seed, precision=APF_FILTER_F64):
+    """e~ = (1/m) sum_c z_c^H rho(l(A)) z_c over m seeded +-1 probes (Sec. 3.4)."""
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    out = C.c_double()
+    ctx.lib.check(ctx.lib.apf_count_estimate(ctx.h, A.h, _ptr(coef), coef.size - 1, float(l1), float(l2),
+                                             int(precision), int(m), int(seed), C.byref(out)), ctx.h)
+    return out.value
 
 
 def filter_apply(ctx, A, coef, l1, l2, X, Y, precision=APF_FILTER_F64):

@@ -221,6 +221,14 @@ void small_inf_norm(apf_ctx* ctx, int64_t p, const T* B, int64_t ldb, double* ou
 // ---- element-wise and reduction kernels (k_misc.cu) ----------------------------
 template <class T>
 void random_block(apf_ctx* ctx, uint64_t seed, uint32_t stream, int64_t n, int64_t p, T* X, int64_t ld);
+// reps copies of an n x m block of +-1 side by side: X[i, r m + c] = -1 when
+// the uniform draw of counter i m + c of (seed, stream) is below 1/2, else +1
+template <class T>
+void rademacher_block(apf_ctx* ctx, uint64_t seed, uint32_t stream, int64_t n, int64_t m, int64_t reps, T* X,
+                      int64_t ld);
+// out[c] = sum_i Re(conj(X[i, c]) Y[i, c]) in FP64 (device), c < p
+template <class T>
+void column_dots(apf_ctx* ctx, int64_t n, int64_t p, const T* X, const T* Y, int64_t ld, double* out);
 template <class TI, class TO>
 void cast_block(apf_ctx* ctx, int64_t n, int64_t p, const TI* X, int64_t ldx, TO* Y, int64_t ldy);
 template <class T>

@@ -113,6 +113,8 @@ void apf_params_default(apf_params* p) {
   p->init_block = nullptr;
   p->init_on_device = 0;
   p->max_degree_cap = 100000;
+  p->mu = 1.8;
+  p->trace_probes = 32;
 }
 
 }  // extern "C"
@@ -660,6 +662,19 @@ apf_status apf_filter_apply(apf_ctx* ctx, const apf_matrix* A, const double* coe
   else
     apf::filter_apply_public<double>(ctx, A, coef, degree, l1, l2, precision, static_cast<const double*>(X), ldx, p,
                                      static_cast<double*>(Y), ldy);
+  APF_CATCH(ctx)
+}
+
+apf_status apf_count_estimate(apf_ctx* ctx, const apf_matrix* A, const double* coef, int32_t degree, double l1,
+                              double l2, int32_t precision, int32_t m, uint64_t seed, double* host_out) {
+  if (!ctx || !A || !coef || degree < 0 || !host_out || m < 1 || m > 8 * APF_MAX_P) return APF_ERR_ARG;
+  if (precision != APF_FILTER_F64 && precision != APF_FILTER_F32) return APF_ERR_ARG;
+  APF_TRY(ctx)
+  bind(ctx);
+  if (A->dtype == APF_C128)
+    *host_out = apf::count_estimate_public<double2>(ctx, A, coef, degree, l1, l2, precision, m, seed);
+  else
+    *host_out = apf::count_estimate_public<double>(ctx, A, coef, degree, l1, l2, precision, m, seed);
   APF_CATCH(ctx)
 }
 

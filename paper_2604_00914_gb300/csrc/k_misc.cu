@@ -88,6 +88,26 @@ void random_block(apf_ctx* ctx, uint64_t seed, uint32_t stream, int64_t n, int64
 template void random_block<double>(apf_ctx*, uint64_t, uint32_t, int64_t, int64_t, double*, int64_t);
 template void random_block<double2>(apf_ctx*, uint64_t, uint32_t, int64_t, int64_t, double2*, int64_t);
 
+template <class T>
+__global__ void k_rademacher_block(uint64_t key, int64_t n, int64_t m, int64_t reps, T* X, int64_t ld) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * m * reps) return;
+  const int64_t i = e / (m * reps), col = e % (m * reps), c = col % m;
+  const double u = sm64_uniform(key, (uint64_t)(i * m + c));
+  X[i * ld + col] = make_val<T>(u < 0.5 ? -1.0 : 1.0, 0.0);
+}
+
+template <class T>
+void rademacher_block(apf_ctx* ctx, uint64_t seed, uint32_t stream, int64_t n, int64_t m, int64_t reps, T* X,
+                      int64_t ld) {
+  if (n * m * reps == 0) return;
+  const uint64_t key = host_mix(seed + 0x9E3779B97F4A7C15ull * ((uint64_t)stream + 1));
+  k_rademacher_block<T><<<grid1d(n * m * reps), 256, 0, ctx->stream>>>(key, n, m, reps, X, ld);
+  count_launch(ctx);
+}
+template void rademacher_block<double>(apf_ctx*, uint64_t, uint32_t, int64_t, int64_t, int64_t, double*, int64_t);
+template void rademacher_block<double2>(apf_ctx*, uint64_t, uint32_t, int64_t, int64_t, int64_t, double2*, int64_t);
+
 // ---- casts and copies -----------------------------------------------------------------
 __device__ __forceinline__ float cvt(double v, float*) { return (float)v; }
 __device__ __forceinline__ float2 cvt(double2 v, float2*) { return make_float2((float)v.x, (float)v.y); }
@@ -269,6 +289,27 @@ __global__ void k_residual_partial(int64_t n, int64_t p, const T* __restrict__ A
   part[(int64_t)blockIdx.y * p + c] = s;
 }
 
+// partial sums of Re(conj(x) y) per column over a band of rows
+template <class T>
+__global__ void k_dot_partial(int64_t n, int64_t p, const T* __restrict__ X, const T* __restrict__ Y, int64_t ld,
+                              int64_t rows_per_block, double* __restrict__ part) {
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_block;
+  const int64_t r1 = min(n, r0 + rows_per_block);
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p) return;
+  double s = 0.0;
+  for (int64_t i = r0; i < r1; ++i) s += re_dot(X[i * ld + c], Y[i * ld + c]);
+  part[(int64_t)blockIdx.y * p + c] = s;
+}
+
+__global__ void k_colsum(int64_t p, int64_t nb, const double* __restrict__ part, double* __restrict__ out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p) return;
+  double s = 0.0;
+  for (int64_t b = 0; b < nb; ++b) s += part[b * p + c];
+  out[c] = s;
+}
+
 __global__ void k_colsum_sqrt(int64_t p, int64_t nb, const double* __restrict__ part, double* __restrict__ out) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p) return;
@@ -300,6 +341,24 @@ template void residual_norms<double>(apf_ctx*, int64_t, int64_t, const double*, 
                                      const double*, double*, float*, double, const int32_t*);
 template void residual_norms<double2>(apf_ctx*, int64_t, int64_t, const double2*, const double2*, int64_t,
                                       const double*, double*, float2*, double, const int32_t*);
+
+template <class T>
+void column_dots(apf_ctx* ctx, int64_t n, int64_t p, const T* X, const T* Y, int64_t ld, double* out) {
+  if (p == 0) return;
+  const int64_t cb = (p + 127) / 128;
+  int64_t nb = (4LL * ctx->num_sms + cb - 1) / cb;
+  if (nb > n) nb = n;
+  if (nb < 1) nb = 1;
+  const int64_t rows = (n + nb - 1) / nb;
+  nb = (n + rows - 1) / rows;
+  if (nb < 1) nb = 1;
+  DBuf part((size_t)nb * p * sizeof(double), ctx->stream, true);
+  k_dot_partial<T><<<dim3((unsigned)cb, (unsigned)nb), 128, 0, ctx->stream>>>(n, p, X, Y, ld, rows, part.as<double>());
+  k_colsum<<<grid1d(p, 128), 128, 0, ctx->stream>>>(p, nb, part.as<double>(), out);
+  count_launch(ctx, 2);
+}
+template void column_dots<double>(apf_ctx*, int64_t, int64_t, const double*, const double*, int64_t, double*);
+template void column_dots<double2>(apf_ctx*, int64_t, int64_t, const double2*, const double2*, int64_t, double*);
 
 // ---- the defect form of the filter -------------------------------------------------------
 // Column c with mu = l1 lam_c + l2 runs the scalar Clenshaw recurrence

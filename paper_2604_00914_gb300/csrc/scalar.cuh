@@ -94,6 +94,9 @@ __host__ __device__ __forceinline__ double abs2(double a) { return a * a; }
 __host__ __device__ __forceinline__ double abs2(double2 a) { return a.x * a.x + a.y * a.y; }
 __host__ __device__ __forceinline__ float abs2(float a) { return a * a; }
 __host__ __device__ __forceinline__ float abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+// Re(conj(a) b)
+__host__ __device__ __forceinline__ double re_dot(double a, double b) { return a * b; }
+__host__ __device__ __forceinline__ double re_dot(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
 // real part
 __host__ __device__ __forceinline__ double real_(double a) { return a; }
 __host__ __device__ __forceinline__ double real_(double2 a) { return a.x; }

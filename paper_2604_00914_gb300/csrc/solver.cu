@@ -777,14 +777,10 @@ struct IntervalState {
   std::vector<double> lam_lock, hw, hr;
   std::vector<double> rec;  // history row of the last iteration
 
-  // set-up (Alg. 4): degrees, coefficients, buffers and the orthonormal initial block
-  void init(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, double a_, double b_, int64_t p_,
-            double l1, double l2, uint32_t stream, SmallWork<T>& sw) {
+  // set-up (Alg. 4): the map of [a, b], the degrees k^(1) and k, the coefficients
+  void setup_filter(const apf_params* prm, double a_, double b_, double l1, double l2) {
     a = a_;
     b = b_;
-    p = p_;
-    const int64_t n = A->n;
-    APF_REQUIRE(p >= 1 && p <= n && p <= APF_MAX_P, APF_ERR_ARG);
     APF_REQUIRE(a < b, APF_ERR_ARG);
     const double am = l1 * a + l2, bm = l1 * b + l2;
     APF_REQUIRE(am > -1.0 && bm < 1.0 && am < bm, APF_ERR_ARG);
@@ -796,6 +792,14 @@ struct IntervalState {
     }
     APF_REQUIRE(k1 >= 0 && kmax <= prm->max_degree_cap, APF_ERR_ARG);
     coef = filter_coefficients(am, bm, kmax, prm->damping, prm->m_d);
+  }
+
+  // set-up (Alg. 4): buffers for subspace size p and the orthonormal initial block
+  void init_block(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, int64_t p_, uint32_t stream,
+                  SmallWork<T>& sw) {
+    p = p_;
+    const int64_t n = A->n;
+    APF_REQUIRE(p >= 1 && p <= n && p <= APF_MAX_P, APF_ERR_ARG);
     ld = block_ld(p);
     const size_t blk = (size_t)n * ld * sizeof(T);
     Vh.alloc(blk, ctx->stream, true);
@@ -941,6 +945,64 @@ static void assemble_result(apf_ctx* ctx, const apf_matrix* A, const std::vector
   APF_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
+// ---- Sec. 3.4: eigenvalue counts and the subspace size ------------------------------------
+// e~_s = (1/m) sum_c z_c^H rho_s(l(A)) z_c for every interval s, with rho_s its
+// filter at the maximum degree and the same m real +-1 probes z_c for all.
+// One batched filter application: the probe block is repeated once per
+// interval, highest degree first.
+template <class T>
+static std::vector<double> count_estimates(apf_ctx* ctx, const apf_matrix* A, int precision, double l1, double l2,
+                                           const std::vector<const std::vector<double>*>& coefs, int64_t m,
+                                           uint64_t seed) {
+  const int64_t n = A->n;
+  const int64_t g = (int64_t)coefs.size();
+  APF_REQUIRE(g >= 1 && m >= 1 && g * m <= 8 * APF_MAX_P, APF_ERR_ARG);
+  std::vector<int> ord((size_t)g);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return coefs[(size_t)u]->size() > coefs[(size_t)v]->size(); });
+  std::vector<double> all;
+  std::vector<int32_t> kc;
+  std::vector<int64_t> coff;
+  for (int s : ord) {
+    const int64_t o = (int64_t)all.size();
+    all.insert(all.end(), coefs[(size_t)s]->begin(), coefs[(size_t)s]->end());
+    for (int64_t c = 0; c < m; ++c) {
+      kc.push_back((int32_t)coefs[(size_t)s]->size() - 1);
+      coff.push_back(o);
+    }
+  }
+  const int64_t w = g * m, ld = block_ld(w);
+  DBuf cd(all.size() * sizeof(double), ctx->stream, false);
+  APF_CUDA(cudaMemcpyAsync(cd.p, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  DBuf Z((size_t)n * ld * sizeof(T), ctx->stream, true), Y((size_t)n * ld * sizeof(T), ctx->stream, true);
+  rademacher_block<T>(ctx, seed, 3u, n, m, g, Z.as<T>(), ld);
+  FilterState<T> fs;
+  fs.init(ctx, A, ld, l1, l2, std::vector<double>(), precision);
+  FilterCount fc;
+  fs.apply_cols(kc, coff, cd.as<double>(), Z.as<T>(), nullptr, nullptr, w, Y.as<T>(), nullptr, nullptr, &fc);
+  DBuf dots((size_t)w * sizeof(double), ctx->stream, false);
+  column_dots<T>(ctx, n, w, Z.as<T>(), Y.as<T>(), ld, dots.as<double>());
+  std::vector<double> h((size_t)w);
+  APF_CUDA(cudaMemcpyAsync(h.data(), dots.p, (size_t)w * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  APF_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (fetch_device_error(ctx) != 0) throw ApfError{APF_ERR_TIMEOUT, "count estimate filter"};
+  std::vector<double> e((size_t)g, 0.0);
+  for (int64_t i = 0; i < g; ++i) {
+    double s = 0.0;
+    for (int64_t c = 0; c < m; ++c) s += h[(size_t)(i * m + c)];
+    e[(size_t)ord[(size_t)i]] = s / (double)m;
+  }
+  return e;
+}
+
+// p = ceil(mu e~), e~ floored at 1, clipped to [1, min(n, APF_MAX_P)]
+static int64_t subspace_size(double e_est, double mu, int64_t n) {
+  const double want = ceil(mu * std::max(e_est, 1.0));
+  int64_t p = want > (double)APF_MAX_P ? (int64_t)APF_MAX_P : (int64_t)want;
+  p = std::min(p, n);
+  return std::max<int64_t>(p, 1);
+}
+
 // ---- Alg. 4 ---------------------------------------------------------------------------
 static double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
@@ -1008,7 +1070,8 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
   using clock = std::chrono::steady_clock;
   const auto t_start = clock::now();
   const int64_t n = A->n;
-  APF_REQUIRE(prm->p >= 1 && prm->p <= n && prm->p <= APF_MAX_P, APF_ERR_ARG);
+  APF_REQUIRE(prm->p >= 0 && prm->p <= n && prm->p <= APF_MAX_P, APF_ERR_ARG);
+  APF_REQUIRE(prm->p > 0 || (prm->init_block == nullptr && prm->mu > 0.0 && prm->trace_probes >= 1), APF_ERR_ARG);
   APF_REQUIRE(prm->a < prm->b, APF_ERR_ARG);
   APF_REQUIRE(prm->max_iter >= 1, APF_ERR_ARG);
   APF_REQUIRE(prm->filter_precision >= APF_FILTER_F64 && prm->filter_precision <= APF_FILTER_F32_DEFECT,
@@ -1018,10 +1081,18 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
 
   // set-up (Alg. 4): bounds, map, degrees, coefficients, initial block
   const Bounds bd = setup_bounds(ctx, A, prm);
-  SmallWork<T> sw;
-  sw.init(prm->p, ctx->stream);
   IntervalState<T> S;
-  S.init(ctx, A, prm, prm->a, prm->b, prm->p, bd.l1, bd.l2, 1u, sw);
+  S.setup_filter(prm, prm->a, prm->b, bd.l1, bd.l2);
+  int64_t p = prm->p;
+  if (p == 0) {  // Sec. 3.4: p = ceil(mu e~) from the estimated count
+    st.trace_estimate = count_estimates<T>(ctx, A, prm->filter_precision, bd.l1, bd.l2, {&S.coef},
+                                           prm->trace_probes, prm->seed)[0];
+    p = subspace_size(st.trace_estimate, prm->mu, n);
+  }
+  st.p_used = p;
+  SmallWork<T> sw;
+  sw.init(p, ctx->stream);
+  S.init_block(ctx, A, prm, p, 1u, sw);
   st.k1 = S.k1;
   st.k_max = S.kmax;
   st.lambda_min = bd.lmin;
@@ -1092,13 +1163,12 @@ static void solve_slices_t(apf_ctx* ctx, const apf_matrix* A, int ns, const doub
   APF_REQUIRE(prm->max_iter >= 1 && prm->init_block == nullptr, APF_ERR_ARG);
   APF_REQUIRE(prm->filter_precision >= APF_FILTER_F64 && prm->filter_precision <= APF_FILTER_F32_DEFECT,
               APF_ERR_ARG);
-  int64_t ptot = 0, pmax = 0;
+  bool any_estimate = false;
   for (int s = 0; s < ns; ++s) {
-    APF_REQUIRE(p[s] >= 1 && a[s] < b[s], APF_ERR_ARG);
-    ptot += p[s];
-    pmax = std::max(pmax, p[s]);
+    APF_REQUIRE(p[s] >= 0 && a[s] < b[s], APF_ERR_ARG);
+    any_estimate = any_estimate || p[s] == 0;
   }
-  APF_REQUIRE(ptot <= n && ptot <= APF_MAX_P, APF_ERR_ARG);
+  APF_REQUIRE(!any_estimate || (prm->mu > 0.0 && prm->trace_probes >= 1), APF_ERR_ARG);
   // slices in ascending order must not overlap
   std::vector<int> by_a((size_t)ns);
   std::iota(by_a.begin(), by_a.end(), 0);
@@ -1108,13 +1178,35 @@ static void solve_slices_t(apf_ctx* ctx, const apf_matrix* A, int ns, const doub
   apf_stats st{};
 
   const Bounds bd = setup_bounds(ctx, A, prm);
+  std::vector<IntervalState<T>> S((size_t)ns);
+  for (int s = 0; s < ns; ++s) S[(size_t)s].setup_filter(prm, a[s], b[s], bd.l1, bd.l2);
+  // Sec. 3.4 for the slices without a size: their counts in one batched filter pass
+  std::vector<int64_t> ps(p, p + ns);
+  if (any_estimate) {
+    std::vector<const std::vector<double>*> cs;
+    std::vector<int> which;
+    for (int s = 0; s < ns; ++s)
+      if (p[s] == 0) { cs.push_back(&S[(size_t)s].coef); which.push_back(s); }
+    const std::vector<double> e = count_estimates<T>(ctx, A, prm->filter_precision, bd.l1, bd.l2, cs,
+                                                     prm->trace_probes, prm->seed);
+    for (size_t i = 0; i < which.size(); ++i) {
+      ps[(size_t)which[i]] = subspace_size(e[i], prm->mu, n);
+      st.trace_estimate += e[i];
+    }
+  }
+  int64_t ptot = 0, pmax = 0;
+  for (int s = 0; s < ns; ++s) {
+    ptot += ps[(size_t)s];
+    pmax = std::max(pmax, ps[(size_t)s]);
+  }
+  APF_REQUIRE(ptot <= n && ptot <= APF_MAX_P, APF_ERR_ARG);
+  st.p_used = ptot;
   SmallWork<T> sw;
   sw.init(pmax, ctx->stream);
-  std::vector<IntervalState<T>> S((size_t)ns);
   std::vector<double> coef_all;
   std::vector<int64_t> coff((size_t)ns);
   for (int s = 0; s < ns; ++s) {
-    S[(size_t)s].init(ctx, A, prm, a[s], b[s], p[s], bd.l1, bd.l2, 1u + (uint32_t)s, sw);
+    S[(size_t)s].init_block(ctx, A, prm, ps[(size_t)s], 1u + (uint32_t)s, sw);
     coff[(size_t)s] = (int64_t)coef_all.size();
     coef_all.insert(coef_all.end(), S[(size_t)s].coef.begin(), S[(size_t)s].coef.end());
     st.k1 = std::max(st.k1, S[(size_t)s].k1);
@@ -1278,6 +1370,17 @@ void filter_apply_defect_public(apf_ctx* ctx, const apf_matrix* A, const double*
   fs.apply(k, Vb.as<T>(), AVb.as<T>(), lam, p, out.as<T>(), nullptr, nullptr, &fc);
   stage_out<T>(ctx, n, p, out.as<T>(), ld, Y, ldy);
 }
+
+template <class T>
+double count_estimate_public(apf_ctx* ctx, const apf_matrix* A, const double* coef, int k, double l1, double l2,
+                             int precision, int64_t m, uint64_t seed) {
+  const std::vector<double> c(coef, coef + k + 1);
+  return count_estimates<T>(ctx, A, precision, l1, l2, {&c}, m, seed)[0];
+}
+template double count_estimate_public<double>(apf_ctx*, const apf_matrix*, const double*, int, double, double, int,
+                                              int64_t, uint64_t);
+template double count_estimate_public<double2>(apf_ctx*, const apf_matrix*, const double*, int, double, double, int,
+                                               int64_t, uint64_t);
 
 template <class T>
 void spmm_public(apf_ctx* ctx, const apf_matrix* A, const T* X, int64_t ldx, int64_t p, T* Y,

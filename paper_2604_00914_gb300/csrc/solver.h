@@ -32,6 +32,9 @@ void filter_apply_defect_public(apf_ctx* ctx, const apf_matrix* A, const double*
                                 double l1, double l2, const T* V, const T* AV, const double* lam,
                                 int64_t ld, int64_t p, T* Y, int64_t ldy);
 template <class T>
+double count_estimate_public(apf_ctx* ctx, const apf_matrix* A, const double* coef, int k, double l1, double l2,
+                             int precision, int64_t m, uint64_t seed);
+template <class T>
 void spmm_public(apf_ctx* ctx, const apf_matrix* A, const T* X, int64_t ldx, int64_t p, T* Y,
                  int64_t ldy);
 template <class T>

@@ -23,6 +23,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 # stream ids: one per kind of random draw
 STREAM_INIT_BLOCK = 1      # initial block V^(0)
 STREAM_LANCZOS = 2         # Lanczos start vector for the spectrum bounds
+STREAM_TRACE = 3           # probe vectors of the eigenvalue-count estimate
 STREAM_POTENTIAL = 10      # on-site disorder / potential values
 STREAM_PHASE = 11          # Peierls phases of the bonds
 STREAM_CENTRES = 12        # Gaussian well centres
@@ -73,3 +74,10 @@ def uniform_block(seed: int, stream: int, n: int, p: int, is_complex: bool) -> n
         return (u[0::2] + 1j * u[1::2]).reshape(n, p)
     idx = np.arange(n * p, dtype=np.uint64)
     return (2.0 * uniform(seed, stream, idx) - 1.0).reshape(n, p)
+
+
+def rademacher_block(seed: int, stream: int, n: int, m: int) -> np.ndarray:
+    """An n x m block of +-1 (real): entry (i, c) is -1 when the uniform draw of
+    counter i*m + c is below 1/2, else +1."""
+    u = uniform(seed, stream, np.arange(int(n) * int(m), dtype=np.uint64)).reshape(int(n), int(m))
+    return np.where(u < 0.5, -1.0, 1.0)

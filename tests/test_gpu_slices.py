@@ -8,7 +8,6 @@ Clenshaw step serves all slices.
 import numpy as np
 import pytest
 
-from oracle import dense
 from synth import matrices
 
 pytestmark = pytest.mark.gpu
@@ -151,7 +150,7 @@ def test_slices_reject_bad_input(B, ctx):
         ([-1.0, -0.5], [0.0, 0.5], [4, 4]),      # overlapping
         ([0.0, -1.0], [0.5, 0.2], [4, 4]),       # overlapping, out of order
         ([-1.0], [-2.0], [4]),                   # a > b
-        ([-1.0, 1.0], [-0.5, 1.5], [4, 0]),      # p = 0
+        ([-1.0, 1.0], [-0.5, 1.5], [4, -1]),     # p < 0 (0 asks for an estimate)
         ([-1.0, 1.0], [-0.5, 1.5], [200, 100]),  # sum(p) > n
     ]
     for a, b, p in bad:

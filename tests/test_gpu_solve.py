@@ -194,7 +194,7 @@ def test_rejects_bad_input(B, ctx):
         B.Matrix.from_csr(ctx, A.n, A.rowptr, bad, A.vals)
     assert ei.value.status == B.APF_ERR_ARG
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
-    for kw in (dict(a=1.0, b=0.0, p=4), dict(a=-0.1, b=0.1, p=0), dict(a=50.0, b=60.0, p=4),
+    for kw in (dict(a=1.0, b=0.0, p=4), dict(a=-0.1, b=0.1, p=-1), dict(a=50.0, b=60.0, p=4),
                dict(a=-0.1, b=0.1, p=A.n + 1)):
         with pytest.raises(B.ApfError) as ei:
             B.solve(ctx, M, B.default_params(**kw))
