@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--filter-only", type=int, default=0,
                     help="time only N applications of the filter kernel (degree --degree) instead of solves")
     ap.add_argument("--degree", type=int, default=20)
+    ap.add_argument("--requests", type=int, default=24, help="serving workload: number of requests")
+    ap.add_argument("--concurrency", type=int, default=4, help="serving workload: worker slots")
     return ap.parse_args()
 
 
@@ -354,6 +356,80 @@ def ours_arm(args, dist):
     ctx.close()
 
 
+def serving_arm(args, dist):
+    """Independent requests (synth.workloads.serving_requests) through the
+    serving loop: Poisson arrivals at 0.8 x the serial capacity measured on a
+    sample, p50/p99 latency and throughput.  Rank 0 only (one GPU)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2604_00914_gb300 import binding as B
+    from synth import rng, workloads
+
+    if dist.rank != 0:
+        return
+    torch.cuda.set_device(dist.local)
+    reqs = workloads.serving_requests(args.requests)
+    mats = [r.matrix() for r in reqs]
+    prms = [B.default_params(a=r.a, b=r.b, p=0, seed=r.seed, filter_precision=B.APF_FILTER_F32_DEFECT,
+                             max_iter=args.max_iter) for r in reqs]
+    # serial capacity: a sample of requests one at a time (after one warm-up)
+    sample = list(range(min(6, len(reqs))))
+    srv = B.Server(dist.local, max_concurrent=1)
+    res, _ = srv.wait(srv.submit(mats[0].n, mats[0].rowptr, mats[0].colidx, mats[0].vals, prms[0]),
+                      allow_no_convergence=True)
+    res and res.close()
+    t0 = time.perf_counter()
+    for i in sample:
+        res, _ = srv.wait(srv.submit(mats[i].n, mats[i].rowptr, mats[i].colidx, mats[i].vals, prms[i]),
+                          allow_no_convergence=True)
+        res and res.close()
+    serial_s = (time.perf_counter() - t0) / len(sample)
+    srv.close()
+    rate = 0.8 / serial_s
+    u = rng.uniform(BASE_ARRIVALS, rng.STREAM_TEST, np.arange(len(reqs), dtype=np.uint64))
+    gaps = -np.log1p(-u) / rate
+    srv = B.Server(dist.local, max_concurrent=args.concurrency)
+    sampler = ClockSampler(dist.local)
+    sampler.start()
+    t0 = time.perf_counter()
+    tickets = []
+    due = 0.0
+    for i, A in enumerate(mats):
+        due += gaps[i]
+        delay = t0 + due - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(A.n, A.rowptr, A.colidx, A.vals, prms[i]))
+    lat, eig, ok = [], 0, 0
+    for t in tickets:
+        res, info = srv.wait(t, allow_no_convergence=True)
+        lat.append(info["latency_ms"])
+        if res is not None:
+            eig += res.count()
+            res.close()
+        ok += info["status"] == 0
+    wall = time.perf_counter() - t0
+    state = srv.state()
+    srv.close()
+    clocks = sampler.stop()
+    lat = np.array(lat)
+    print(json.dumps({
+        "metric": "serving latency (p50/p99)", "mode": "serving", "requests": len(reqs), "converged": ok,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "serial_ms_per_request": 1e3 * serial_s,
+        "arrival_rate_per_s": rate, "throughput_requests_per_s": len(reqs) / wall,
+        "eigenpairs_per_s": eig / wall, "concurrency": args.concurrency,
+        "peak_running": state["peak_running"], "peak_in_flight_bytes": state["peak_in_flight_bytes"],
+        "data": "synthetic", "clocks": clocks,
+        "config": {"workload": "serving", "n_range": [1e4, 1e5], "target_counts": [8, 64],
+                   "p": "estimated (Sec. 3.4)", "precision": "f32_defect"}}), flush=True)
+
+
+# seed of the serving workload's arrival times
+BASE_ARRIVALS = 20260406
+
+
 def filter_only(args, dist, B, ctx, M, A, w, peak, peak_kind):
     """Time N applications of the FP32 filter recurrence of degree `--degree` on
     the workload's matrix and block width (the dominant kernel alone)."""
@@ -383,6 +459,8 @@ def main():
     try:
         if args.impl == "reference":
             reference_arm(args, dist)
+        elif args.workload == "serving":
+            serving_arm(args, dist)
         else:
             ours_arm(args, dist)
     finally:

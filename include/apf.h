@@ -162,6 +162,17 @@ apf_status apf_matrix_create_sell(apf_ctx* ctx, int64_t n, int32_t C, int32_t si
                                   const int32_t* chunk_len, const int32_t* colidx,
                                   const void* vals, int32_t dtype, apf_matrix** out);
 apf_status apf_matrix_destroy(apf_matrix* A);
+/* The Clenshaw step kernel of the FP32 filter (Alg. 2) for this matrix.  By
+ * default (kind 0) an autotuner times the compiled variants on the first
+ * filter application at each block width and keeps the fastest.  Every
+ * variant does the same operations in the same order, so the choice changes
+ * the time, never the result.  Pin one instead: kind 1 = SELL-8, one step per
+ * launch; 2 = SELL-8, two steps per pass over a banded (reverse Cuthill-McKee)
+ * copy; 3 = CSR.  (G, VPT) = lanes per row x 16-byte vectors per lane, (0, 0)
+ * for the shape with the fewest idle lanes.  Where a pinned kind does not
+ * apply (matrix, width) it falls back 2 -> 1 -> 3.  APF_ERR_ARG for a kind
+ * outside 0..3. */
+apf_status apf_matrix_set_filter_kernel(apf_matrix* A, int32_t kind, int32_t G, int32_t VPT);
 apf_status apf_matrix_info(const apf_matrix* A, int64_t* n, int64_t* nnz, int32_t* dtype);
 
 /* ---- solve -------------------------------------------------------------- */
@@ -209,6 +220,53 @@ apf_status apf_result_stats(const apf_result* r, apf_stats* out);
  * Returns the number of records in *count. */
 apf_status apf_result_history(const apf_result* r, double* host_out, int32_t cap, int32_t* count);
 apf_status apf_result_destroy(apf_result* r);
+
+/* ---- serving: many solves on one GPU -------------------------------------- */
+/* The paper solves one problem at a time; this loop runs independent
+ * requests (Sec. 1: slices and problems need no communication) concurrently
+ * on one device.  Requests are admitted in arrival order when their
+ * estimated device footprint fits in the budget left by the running ones (or
+ * when none runs); each runs on its own context and CUDA stream, so the
+ * running solves' kernels interleave.  A request's result does not depend on
+ * what runs beside it. */
+typedef struct apf_server apf_server;
+
+typedef struct {
+  int32_t status;          /* the solve's apf_status */
+  int32_t worker;          /* worker slot that ran it */
+  double queue_ms;         /* submit -> admission */
+  double run_ms;           /* admission -> done (ingest + solve) */
+  double latency_ms;       /* submit -> done */
+  int64_t footprint_bytes; /* device bytes reserved at admission (estimate) */
+} apf_request_info;
+
+typedef struct {
+  int32_t queued, running, peak_running, workers;
+  int64_t in_flight_bytes, peak_in_flight_bytes, budget_bytes, completed;
+} apf_server_info;
+
+/* Start `max_concurrent` (1..64) worker threads on `device`.  hbm_budget_bytes:
+ * device bytes the running requests may reserve; 0 means 90 % of the memory
+ * free at creation. */
+apf_status apf_server_create(apf_server** out, int32_t device, int32_t max_concurrent,
+                             int64_t hbm_budget_bytes);
+/* Queue one solve of the n x n Hermitian matrix (host CSR, both triangles,
+ * dtype APF_R64 or APF_C128; the arrays are copied) with `params` (p = 0
+ * estimates the subspace size; init_block must be NULL).  *ticket identifies
+ * the request.  APF_ERR_OOM when its footprint estimate alone exceeds the
+ * budget. */
+apf_status apf_server_submit(apf_server* s, int64_t n, int64_t nnz, const int64_t* rowptr,
+                             const int32_t* colidx, const void* vals, int32_t dtype,
+                             const apf_params* params, int64_t* ticket);
+/* Block until the request is done; return its status.  *out receives its
+ * result (as apf_solve gives it; NULL when the solve failed), which owns the
+ * request's context: apf_result_destroy releases both.  `info` (nullable)
+ * receives the request's times.  A ticket can be waited for once. */
+apf_status apf_server_wait(apf_server* s, int64_t ticket, apf_result** out, apf_request_info* info);
+apf_status apf_server_state(apf_server* s, apf_server_info* out);
+/* Finish every queued request, stop the workers, free the results nobody
+ * waited for.  Results already handed out stay valid. */
+apf_status apf_server_destroy(apf_server* s);
 
 /* ---- the steps of the path, callable one by one (device buffers) ---------- */
 

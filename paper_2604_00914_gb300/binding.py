@@ -75,6 +75,28 @@ class apf_stats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class apf_request_info(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("worker", C.c_int32),
+        ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double),
+        ("footprint_bytes", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class apf_server_info(C.Structure):
+    _fields_ = [
+        ("queued", C.c_int32), ("running", C.c_int32), ("peak_running", C.c_int32), ("workers", C.c_int32),
+        ("in_flight_bytes", C.c_int64), ("peak_in_flight_bytes", C.c_int64), ("budget_bytes", C.c_int64),
+        ("completed", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class ApfError(RuntimeError):
     def __init__(self, status, msg=""):
         super().__init__(f"apf status {status}: {msg}")
@@ -104,6 +126,12 @@ SIGNATURES = {
     "apf_solve_slices": (_I32, [_P, _P, _I32, _P, _P, _P, C.POINTER(apf_params), C.POINTER(_P)]),
     "apf_result_slice_counts": (_I32, [_P, _I32, _P]),
     "apf_result_count": (_I32, [_P, C.POINTER(_I64)]),
+    "apf_matrix_set_filter_kernel": (_I32, [_P, _I32, _I32, _I32]),
+    "apf_server_create": (_I32, [C.POINTER(_P), _I32, _I32, _I64]),
+    "apf_server_submit": (_I32, [_P, _I64, _I64, _P, _P, _P, _I32, C.POINTER(apf_params), C.POINTER(_I64)]),
+    "apf_server_wait": (_I32, [_P, _I64, C.POINTER(_P), C.POINTER(apf_request_info)]),
+    "apf_server_state": (_I32, [_P, C.POINTER(apf_server_info)]),
+    "apf_server_destroy": (_I32, [_P]),
     "apf_result_eigvals": (_I32, [_P, _P]),
     "apf_result_eigvecs": (_I32, [_P, _P, _I64, _I32]),
     "apf_result_residuals": (_I32, [_P, _P]),
@@ -244,6 +272,10 @@ class Matrix:
                                                      _ptr(chunk_len), _ptr(colidx), _ptr(vals), dt, C.byref(h)), ctx.h)
         return cls(ctx, h, int(n), dt)
 
+    def set_filter_kernel(self, kind, G=0, VPT=0):
+        """Pin the FP32 Clenshaw step kernel (0 = autotune, 1 = SELL, 2 = SELL two-step, 3 = CSR)."""
+        self.ctx.lib.check(self.ctx.lib.apf_matrix_set_filter_kernel(self.h, int(kind), int(G), int(VPT)))
+
     def close(self):
         if self.h and self.ctx.h:
             self.ctx.lib.apf_matrix_destroy(self.h)
@@ -325,7 +357,7 @@ class Result:
         return [dict(zip(HISTORY_FIELDS, buf[6 * i:6 * i + 6])) for i in range(cnt.value)]
 
     def close(self):
-        if self.h and self.ctx.h:
+        if self.h and (self.ctx.h or getattr(self.ctx, "owns_results", False)):
             self.ctx.lib.apf_result_destroy(self.h)
         self.h = None
 
@@ -360,6 +392,69 @@ def solve_slices(ctx: Context, A: Matrix, a, b, p, params: apf_params, allow_no_
         return Result(ctx, h, st)
     ctx.lib.check(st, ctx.h)
     return Result(ctx, h, st)
+
+
+class _RequestOwner:
+    """Stands in for the context of a serving result: such a result owns its
+    own native context, so it stays valid after the server is gone."""
+    owns_results = True
+    h = None
+
+    def __init__(self, lib):
+        self.lib = lib
+
+    def _adopt(self, obj):
+        pass
+
+
+class Server:
+    """apf_server_*: concurrent solves of independent requests on one device."""
+
+    def __init__(self, device=0, max_concurrent=4, hbm_budget_bytes=0, lib=None):
+        self.lib = lib or Library.load()
+        h = C.c_void_p()
+        self.lib.check(self.lib.apf_server_create(C.byref(h), int(device), int(max_concurrent),
+                                                  int(hbm_budget_bytes)))
+        self.h = h
+
+    def submit(self, n, rowptr, colidx, vals, params):
+        is_c = np.iscomplexobj(vals)
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.complex128 if is_c else np.float64)
+        t = C.c_int64()
+        self.lib.check(self.lib.apf_server_submit(self.h, int(n), int(colidx.shape[0]), _ptr(rowptr), _ptr(colidx),
+                                                  _ptr(vals), APF_C128 if is_c else APF_R64, C.byref(params),
+                                                  C.byref(t)))
+        return t.value
+
+    def wait(self, ticket, allow_no_convergence=False):
+        """(Result or None, info dict) of a finished request."""
+        h = C.c_void_p()
+        info = apf_request_info()
+        st = self.lib.apf_server_wait(self.h, int(ticket), C.byref(h), C.byref(info))
+        res = Result(_RequestOwner(self.lib), h, st) if h.value else None
+        if st != APF_OK and not (st == APF_ERR_NO_CONVERGENCE and allow_no_convergence):
+            if res is not None:
+                res.close()
+            self.lib.check(st)
+        return res, info.as_dict()
+
+    def state(self):
+        s = apf_server_info()
+        self.lib.check(self.lib.apf_server_state(self.h, C.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self.h:
+            self.lib.apf_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- the steps one by one ---------------------------------------------------------------

@@ -65,7 +65,7 @@ def build(verbose_ptxas: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
     if (not os.path.exists(LIB) or verbose_ptxas
             or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)):
-        cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -81,8 +81,10 @@ struct apf_matrix {
   int64_t psell_slots = 0;
   int64_t psell_bw = 0;
   // autotuned Clenshaw-step shape per (element size, vectors per row):
-  // value = kind * 10000 + G * 100 + VPT, kind 1 = SELL, 0 = CSR
+  // value = kind * 10000 + G * 100 + VPT, kind 1 = SELL, 2 = SELL two-step, 0 = CSR
   std::vector<std::pair<int64_t, int>> tune_cache;
+  // a pinned kernel (apf_matrix_set_filter_kernel): kind 0 = autotune
+  int pin_kind = 0, pin_G = 0, pin_VPT = 0;
 };
 
 namespace apf {

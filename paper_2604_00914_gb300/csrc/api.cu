@@ -558,6 +558,15 @@ apf_status apf_result_slice_counts(const apf_result* r, int32_t nslices, int64_t
   return APF_OK;
 }
 
+apf_status apf_matrix_set_filter_kernel(apf_matrix* A, int32_t kind, int32_t G, int32_t VPT) {
+  if (!A || kind < 0 || kind > 3 || G < 0 || VPT < 0) return APF_ERR_ARG;
+  A->pin_kind = kind;
+  A->pin_G = G;
+  A->pin_VPT = VPT;
+  A->tune_cache.clear();
+  return APF_OK;
+}
+
 apf_status apf_result_count(const apf_result* r, int64_t* e) {
   if (!r || !e) return APF_ERR_ARG;
   *e = r->e;
@@ -615,11 +624,13 @@ apf_status apf_result_history(const apf_result* r, double* host_out, int32_t cap
 
 apf_status apf_result_destroy(apf_result* r) {
   if (!r) return APF_OK;
+  apf_ctx* owned = r->owns_ctx ? r->ctx : nullptr;
   if (r->ctx) {
     cudaSetDevice(r->ctx->device);
     cudaStreamSynchronize(r->ctx->stream);
   }
   delete r;
+  if (owned) apf_destroy(owned);
   return APF_OK;
 }
 

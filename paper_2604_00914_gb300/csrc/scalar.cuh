@@ -89,6 +89,38 @@ __host__ __device__ __forceinline__ void madd_conj(double2& acc, double2 a, doub
   acc.y = fma(a.x, b.y, acc.y);
   acc.y = fma(-a.y, b.x, acc.y);
 }
+// One output of a Clenshaw step, alpha acc - v + f y (terms without Vin or Y
+// dropped), with every rounding fixed by explicit round-to-nearest operations
+// so that no kernel variant depends on the compiler's choice of fusions:
+// r = fma(alpha, acc, -v) (or alpha acc, exact for alpha = 1, 2), then
+// r = fma(f, y, r).  Complex values: the same on each component.
+template <class R>
+__device__ __forceinline__ R fma_rn(R a, R b, R c);
+template <> __device__ __forceinline__ float fma_rn<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double fma_rn<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <class R>
+__device__ __forceinline__ R mul_rn(R a, R b);
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+template <class R>
+__device__ __forceinline__ R step_comp(R acc, R alpha, bool hv, R v, bool hy, R f, R y) {
+  const R r = hv ? fma_rn<R>(alpha, acc, -v) : mul_rn<R>(alpha, acc);
+  return hy ? fma_rn<R>(f, y, r) : r;
+}
+__device__ __forceinline__ float step_out(float acc, float al, bool hv, float v, bool hy, float f, float y) {
+  return step_comp<float>(acc, al, hv, v, hy, f, y);
+}
+__device__ __forceinline__ double step_out(double acc, double al, bool hv, double v, bool hy, double f, double y) {
+  return step_comp<double>(acc, al, hv, v, hy, f, y);
+}
+__device__ __forceinline__ float2 step_out(float2 acc, float al, bool hv, float2 v, bool hy, float f, float2 y) {
+  return make_float2(step_comp<float>(acc.x, al, hv, v.x, hy, f, y.x), step_comp<float>(acc.y, al, hv, v.y, hy, f, y.y));
+}
+__device__ __forceinline__ double2 step_out(double2 acc, double al, bool hv, double2 v, bool hy, double f, double2 y) {
+  return make_double2(step_comp<double>(acc.x, al, hv, v.x, hy, f, y.x),
+                      step_comp<double>(acc.y, al, hv, v.y, hy, f, y.y));
+}
+
 // |a|^2
 __host__ __device__ __forceinline__ double abs2(double a) { return a * a; }
 __host__ __device__ __forceinline__ double abs2(double2 a) { return a.x * a.x + a.y * a.y; }

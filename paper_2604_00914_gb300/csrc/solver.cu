@@ -157,9 +157,16 @@ struct Stepper {
   void operator()(const S* W, const S* Vin, const S* Y, int64_t ncols, const Real* coef_col,
                   Real coef_scalar, Real alpha, S* Out) const {
     if (kind >= 1) {
-      if constexpr (sizeof(Real) == 4)
-        clenshaw_step_sell<S, S>(ctx, G, VPT, A->n, A->sell_chunk_ptr, A->sell_col, sell_vals,
-                                 A->sell_lmax, W, Vin, Y, ld, ncols, coef_col, coef_scalar, alpha, Out);
+      // the two-step form keeps its blocks in the permuted row order: its
+      // single steps (the last one or two) must use the permuted copy too
+      if constexpr (sizeof(Real) == 4) {
+        if (kind == 2 && A->perm)
+          clenshaw_step_sell<S, S>(ctx, G, VPT, A->n, A->psell_chunk_ptr, A->psell_col, psell_vals,
+                                   A->psell_lmax, W, Vin, Y, ld, ncols, coef_col, coef_scalar, alpha, Out);
+        else
+          clenshaw_step_sell<S, S>(ctx, G, VPT, A->n, A->sell_chunk_ptr, A->sell_col, sell_vals,
+                                   A->sell_lmax, W, Vin, Y, ld, ncols, coef_col, coef_scalar, alpha, Out);
+      }
     } else if (G > 0) {
       if constexpr (sizeof(Real) == 4)
         clenshaw_step_shape<S, S>(ctx, G, VPT, A->n, A->rowptr, A->colidx, csr_vals, W, Vin, Y, ld,
@@ -170,6 +177,59 @@ struct Stepper {
     }
   }
 };
+
+constexpr int kNumSellShapes = (int)(sizeof(kSellShapes) / sizeof(kSellShapes[0]));
+
+template <class S>
+static bool sell_shape_fits(const Stepper<S>& st, int G, int VPT, int nvec) {
+  if (G * VPT < nvec) return false;
+  const int R = 256 / G;
+  return (size_t)R * st.ld * sizeof(S) * 2 + (size_t)R * st.A->sell_lmax * 12 <= 180 * 1024 &&
+         (size_t)R * st.ld * sizeof(S) * 2 + (size_t)R * (st.A->perm ? st.A->psell_lmax : st.A->sell_lmax) * 12 <=
+             180 * 1024;
+}
+
+// The kernel pinned on the matrix, without timing: kind 2 (two steps per
+// pass) falls back to 1 (SELL) and 1 to CSR where they do not apply; the
+// pinned (G, VPT) when it covers the width, else the shape with the fewest
+// idle vector slots (ties: more vectors per lane).
+template <class S>
+static void pinned_shape(Stepper<S>& st, int nvec) {
+  const apf_matrix* A = st.A;
+  int kind = A->pin_kind == 3 ? 0 : A->pin_kind;
+  if (kind >= 1 && !(A->sell_ok && nvec <= 256)) kind = 0;
+  if (kind == 2) {
+    const int R = 256 / (A->pin_G > 0 ? A->pin_G : 8);
+    if (st.seg_count == nullptr || (int64_t)R * 4 >= A->n) kind = 1;
+  }
+  if (kind == 0) {
+    st.kind = 0;
+    const int nv = nvec > 256 ? 256 : nvec;
+    choose_group(nv, &st.G, &st.VPT);
+    static const int csrG[] = {4, 8, 16, 32};
+    bool ok = false;
+    for (int g : csrG) ok = ok || g == A->pin_G;
+    const bool vok = A->pin_VPT >= 1 && A->pin_VPT <= 8 && A->pin_VPT != 7;
+    if (ok && vok && A->pin_G * A->pin_VPT >= nv) { st.G = A->pin_G; st.VPT = A->pin_VPT; }
+    return;
+  }
+  int bg = 0, bv = 0;
+  for (int i = 0; i < kNumSellShapes; ++i) {
+    const int g = kSellShapes[i].G, v = kSellShapes[i].VPT;
+    if (!sell_shape_fits(st, g, v, nvec)) continue;
+    if (g == A->pin_G && v == A->pin_VPT) { bg = g; bv = v; break; }
+    if (bg == 0 || g * v < bg * bv || (g * v == bg * bv && v > bv)) { bg = g; bv = v; }
+  }
+  if (bg == 0) {  // no SELL shape fits: CSR
+    st.kind = 0;
+    choose_group(nvec > 256 ? 256 : nvec, &st.G, &st.VPT);
+    return;
+  }
+  if (kind == 2 && (int64_t)(256 / bg) * 4 >= A->n) kind = 1;
+  st.kind = kind;
+  st.G = bg;
+  st.VPT = bv;
+}
 
 // Autotuner: time each candidate shape on the live buffers (one warm-up and
 // three timed launches) and keep the fastest per (element size, ld, width) in
@@ -184,6 +244,10 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
   if constexpr (sizeof(Real) != 4) return;
   const int nvec = (int)((p + E - 1) / E);
   apf_matrix* A = const_cast<apf_matrix*>(st.A);
+  if (A->pin_kind != 0) {
+    pinned_shape(st, nvec);
+    return;
+  }
   const int64_t key = ((int64_t)sizeof(S) << 48) | ((int64_t)st.ld << 16) | nvec;
   for (auto& kv : A->tune_cache)
     if (kv.first == key) {
@@ -200,20 +264,19 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
   // natural one: a matrix with a SELL copy always uses SELL
   if (!(A->sell_ok && nvec <= 256)) cands.push_back({0, g0, v0});
   if (A->sell_ok && nvec <= 256) {
-    static const int shapes[][2] = {{8, 1}, {8, 2}, {8, 3}, {8, 4}, {16, 2}, {16, 3}, {16, 4}, {16, 5},
-                                    {16, 6}, {32, 2}, {32, 3}, {32, 4}, {32, 5}, {32, 6}, {32, 8}};
+    const auto& shapes = kSellShapes;
     // shapes with at most 40 % idle vector slots, or the least idle one
     int least = -1;
-    for (int i = 0; i < (int)(sizeof(shapes) / sizeof(shapes[0])); ++i) {
-      const int gv = shapes[i][0] * shapes[i][1];
-      if (gv >= nvec && (least < 0 || gv < shapes[least][0] * shapes[least][1])) least = i;
+    for (int i = 0; i < kNumSellShapes; ++i) {
+      const int gv = shapes[i].G * shapes[i].VPT;
+      if (gv >= nvec && (least < 0 || gv < shapes[least].G * shapes[least].VPT)) least = i;
     }
-    for (int i = 0; i < (int)(sizeof(shapes) / sizeof(shapes[0])); ++i) {
-      const int g = shapes[i][0], v = shapes[i][1];
+    for (int i = 0; i < kNumSellShapes; ++i) {
+      const int g = shapes[i].G, v = shapes[i].VPT;
       if (g * v < nvec) continue;
       if ((double)(g * v - nvec) / (g * v) > 0.4 && i != least) continue;
       const int R = 256 / g;
-      if ((size_t)R * st.ld * sizeof(S) * 2 + (size_t)R * A->sell_lmax * 12 > 180 * 1024) continue;
+      if (!sell_shape_fits(st, g, v, nvec)) continue;
       cands.push_back({1, g, v});
       // two steps per pass when the rows a tile depends on stay within reach of L2
       const int64_t bwp = A->perm ? A->psell_bw : A->sell_bw;
@@ -261,6 +324,7 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
   st.kind = pick.kind;
   st.G = pick.G;
   st.VPT = pick.VPT;
+  if (verbose) fprintf(stderr, "apf tune: nvec %d picked kind %d G %d VPT %d\n", nvec, pick.kind, pick.G, pick.VPT);
   A->tune_cache.push_back({key, pick.kind * 10000 + pick.G * 100 + pick.VPT});
 }
 

@@ -14,6 +14,7 @@ struct apf_result {
   std::vector<double> history;    // 6 doubles per iteration
   std::vector<int64_t> slice_counts;  // per slice, input order (apf_solve_slices)
   apf_stats stats{};
+  bool owns_ctx = false;  // a serving request's result: destroying it destroys its context
 };
 
 namespace apf {

@@ -98,17 +98,14 @@ k_clenshaw_step(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __
     const int vi = lane + q * G;
     if (vi >= nvec) continue;
     Pack16<T> y, v, o;
+    y.u = make_uint4(0u, 0u, 0u, 0u);
+    v.u = y.u;
     if (Y) y.u = __ldcs(reinterpret_cast<const uint4*>(Y + rbase) + vi);
     if (Vin) v.u = __ldcs(reinterpret_cast<const uint4*>(Vin + rbase) + vi);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      T r = rmul(alpha, acc[q][e]);
-      if (Vin) r = sub(r, v.t[e]);
-      if (Y) {
-        const Real f = coef_col ? coef_col[vi * E + e] : coef_scalar;
-        r = add(r, rmul(f, y.t[e]));
-      }
-      o.t[e] = r;
+      const Real f = Y ? (coef_col ? coef_col[vi * E + e] : coef_scalar) : (Real)0;
+      o.t[e] = step_out(acc[q][e], alpha, Vin != nullptr, v.t[e], Y != nullptr, f, y.t[e]);
     }
     reinterpret_cast<uint4*>(Out + rbase)[vi] = o.u;
   }

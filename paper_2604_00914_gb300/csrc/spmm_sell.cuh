@@ -18,6 +18,8 @@
 // Every wait on the mbarrier is bounded in time; on expiry the kernel records
 // DEV_BARRIER_TIMEOUT, waits (bounded) for its copies and returns.
 #pragma once
+#include <atomic>
+
 #include "spmm_impl.cuh"
 
 namespace apf {
@@ -164,7 +166,10 @@ __device__ __forceinline__ bool sell_tile(
       const int vi = lane + q * G;
       if (vi < nvec) {
         Pack16<T> w;
-        if constexpr (COHERENT_W) w.u = wrow[vi];  // written earlier in this launch: coherent load
+        // written earlier in this launch by other CTAs: load from L2, never
+        // from this SM's L1, which may hold a line fetched before the rows
+        // next to the waited-for range were written
+        if constexpr (COHERENT_W) w.u = __ldcg(wrow + vi);
         else w.u = __ldg(wrow + vi);
 #pragma unroll
         for (int e = 0; e < E; ++e) madd(acc[q][e], v, w.t[e]);
@@ -178,17 +183,14 @@ __device__ __forceinline__ bool sell_tile(
     const int vi = lane + q * G;
     if (vi >= nvec) continue;
     Pack16<T> y, v, o;
+    y.u = make_uint4(0u, 0u, 0u, 0u);
+    v.u = y.u;
     if (Y) y.u = reinterpret_cast<const uint4*>(ys)[vi];
     if (Vin) v.u = reinterpret_cast<const uint4*>(vs)[vi];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      T r = rmul(alpha, acc[q][e]);
-      if (Vin) r = sub(r, v.t[e]);
-      if (Y) {
-        const Real f = coef_col ? coef_col[vi * E + e] : coef_scalar;
-        r = add(r, rmul(f, y.t[e]));
-      }
-      o.t[e] = r;
+      const Real f = Y ? (coef_col ? coef_col[vi * E + e] : coef_scalar) : (Real)0;
+      o.t[e] = step_out(acc[q][e], alpha, Vin != nullptr, v.t[e], Y != nullptr, f, y.t[e]);
     }
     reinterpret_cast<uint4*>(Out + row * ld)[vi] = o.u;
   }
@@ -345,6 +347,17 @@ static const SellShape kSellShapes[] = {{8, 1}, {8, 2}, {8, 3}, {8, 4}, {16, 2},
                                         {16, 5}, {16, 6}, {32, 2}, {32, 3}, {32, 4}, {32, 5}, {32, 6},
                                         {32, 8}};
 
+// Opt a kernel into 200 KB of dynamic shared memory, once per device; safe to
+// call from several host threads (contexts may live on different threads).
+template <auto Kern>
+inline void allow_large_smem(int device) {
+  static std::atomic<uint64_t> done{0};
+  const uint64_t bit = 1ull << (device & 63);
+  if (done.load(std::memory_order_acquire) & bit) return;
+  APF_CUDA(cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  done.fetch_or(bit, std::memory_order_release);
+}
+
 template <class T, class TA>
 void clenshaw_sell_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* chunk_ptr,
                           const int32_t* scol, const TA* sval, int lmax, const T* W, const T* Vin,
@@ -365,11 +378,7 @@ void clenshaw_sell_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t
 #define APF_SELL_CASE(GG, VV)                                                                        \
   if (G == GG && VPT == VV) {                                                                        \
     auto kern = k_clenshaw_sell<T, TA, GG, VV>;                                                      \
-    static bool attr_set = false;                                                                    \
-    if (!attr_set) {                                                                                 \
-      APF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); \
-      attr_set = true;                                                                               \
-    }                                                                                                \
+    allow_large_smem<k_clenshaw_sell<T, TA, GG, VV>>(ctx->device);                                   \
     kern<<<grid, 256, smem, ctx->stream>>>(n, chunk_ptr, scol, sval, lmax, W, Vin, Y, ld, nvec,      \
                                            coef_col, coef_scalar, alpha, Out, ctx->d_err);           \
     launched = true;                                                                                 \
@@ -427,11 +436,7 @@ void clenshaw_sell_pair_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const in
 #define APF_PAIR_CASE(GG, VV)                                                                         \
   if (G == GG && VPT == VV) {                                                                         \
     auto kern = k_clenshaw_sell_pair<T, TA, GG, VV>;                                                  \
-    static bool attr_set = false;                                                                     \
-    if (!attr_set) {                                                                                  \
-      APF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));  \
-      attr_set = true;                                                                                \
-    }                                                                                                 \
+    allow_large_smem<k_clenshaw_sell_pair<T, TA, GG, VV>>(ctx->device);                               \
     int per_sm = 0;                                                                                   \
     APF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));                \
     APF_REQUIRE(per_sm >= 1, APF_ERR_ARG);                                                            \

@@ -102,3 +102,47 @@ WORKLOADS = {
     "anderson3d_c_64": anderson3d_c_64,
     "anderson3d_c_48": anderson3d_c_48,
 }
+
+
+@dataclass
+class Request:
+    """One serving request: a matrix recipe, an interval, p = 0 (estimated)."""
+    dim: int
+    L: int
+    W: float
+    is_complex: bool
+    seed: int
+    a: float
+    b: float
+    target: int
+
+    def matrix(self) -> matrices.CSR:
+        return matrices.anderson(self.L, self.dim, self.W, self.seed, complex_phases=self.is_complex)
+
+
+def serving_requests(count: int = 24, seed: int = BASE_SEED + 5, n_lo: float = 1e4,
+                     n_hi: float = 1e5) -> list:
+    """A seeded stream of independent eigenproblems: Anderson models in 2D or
+    3D (50/50), real or complex (50/50), n log-uniform in [n_lo, n_hi]
+    (L = round(n^(1/d))), disorder W ~ U[1, 6], a target count U{8..64} and an
+    interval of that many states under a flat density of states over the
+    Gershgorin range [-2d - W/2, 2d + W/2], centred uniformly in the middle
+    half of the band.  The true count differs from the target where the
+    density is not flat; the requests leave p = 0 (estimated)."""
+    import math
+    import numpy as np
+    from . import rng
+    u = rng.uniform(seed, rng.STREAM_TEST, np.arange(7 * count, dtype=np.uint64)).reshape(count, 7)
+    out = []
+    for i in range(count):
+        dim = 2 if u[i, 0] < 0.5 else 3
+        is_c = bool(u[i, 1] < 0.5)
+        n = math.exp(math.log(n_lo) + u[i, 2] * (math.log(n_hi) - math.log(n_lo)))
+        L = max(3, int(round(n ** (1.0 / dim))))
+        W = 1.0 + 5.0 * u[i, 3]
+        target = 8 + int(57 * u[i, 4])
+        span = 4.0 * dim + W
+        half = 0.5 * target * span / (L ** dim)
+        centre = (u[i, 5] - 0.5) * 0.5 * span
+        out.append(Request(dim, L, W, is_c, seed + 1 + i, centre - half, centre + half, target))
+    return out
