@@ -358,8 +358,10 @@ def ours_arm(args, dist):
 
 def serving_arm(args, dist):
     """Independent requests (synth.workloads.serving_requests) through the
-    serving loop: Poisson arrivals at 0.8 x the serial capacity measured on a
-    sample, p50/p99 latency and throughput.  Rank 0 only (one GPU)."""
+    serving loop: first every request once, one at a time (the serial
+    capacity), then all of them again with Poisson arrivals at 0.8 x that
+    capacity and `--concurrency` worker slots; p50/p99 latency, throughput and
+    whether each result equals its serial run.  Rank 0 only (one GPU)."""
     import math
     import numpy as np
     import torch
@@ -373,18 +375,21 @@ def serving_arm(args, dist):
     mats = [r.matrix() for r in reqs]
     prms = [B.default_params(a=r.a, b=r.b, p=0, seed=r.seed, filter_precision=B.APF_FILTER_F32_DEFECT,
                              max_iter=args.max_iter) for r in reqs]
-    # serial capacity: a sample of requests one at a time (after one warm-up)
-    sample = list(range(min(6, len(reqs))))
+    # serial capacity: every request one at a time (after one warm-up)
     srv = B.Server(dist.local, max_concurrent=1)
     res, _ = srv.wait(srv.submit(mats[0].n, mats[0].rowptr, mats[0].colidx, mats[0].vals, prms[0]),
                       allow_no_convergence=True)
-    res and res.close()
+    if res is not None:
+        res.close()
+    serial_lam, serial_lat = [], []
     t0 = time.perf_counter()
-    for i in sample:
-        res, _ = srv.wait(srv.submit(mats[i].n, mats[i].rowptr, mats[i].colidx, mats[i].vals, prms[i]),
-                          allow_no_convergence=True)
-        res and res.close()
-    serial_s = (time.perf_counter() - t0) / len(sample)
+    for i, A in enumerate(mats):
+        res, info = srv.wait(srv.submit(A.n, A.rowptr, A.colidx, A.vals, prms[i]), allow_no_convergence=True)
+        serial_lat.append(info["latency_ms"])
+        serial_lam.append(res.eigvals() if res is not None else None)
+        if res is not None:
+            res.close()
+    serial_s = (time.perf_counter() - t0) / len(mats)
     srv.close()
     rate = 0.8 / serial_s
     u = rng.uniform(BASE_ARRIVALS, rng.STREAM_TEST, np.arange(len(reqs), dtype=np.uint64))
@@ -401,12 +406,13 @@ def serving_arm(args, dist):
         if delay > 0:
             time.sleep(delay)
         tickets.append(srv.submit(A.n, A.rowptr, A.colidx, A.vals, prms[i]))
-    lat, eig, ok = [], 0, 0
-    for t in tickets:
+    lat, eig, ok, same = [], 0, 0, 0
+    for i, t in enumerate(tickets):
         res, info = srv.wait(t, allow_no_convergence=True)
         lat.append(info["latency_ms"])
         if res is not None:
             eig += res.count()
+            same += int(serial_lam[i] is not None and np.array_equal(serial_lam[i], res.eigvals()))
             res.close()
         ok += info["status"] == 0
     wall = time.perf_counter() - t0
@@ -418,6 +424,8 @@ def serving_arm(args, dist):
         "metric": "serving latency (p50/p99)", "mode": "serving", "requests": len(reqs), "converged": ok,
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "serial_ms_per_request": 1e3 * serial_s,
+        "serial_p50_ms": float(np.percentile(serial_lat, 50)), "serial_p99_ms": float(np.percentile(serial_lat, 99)),
+        "same_as_serial": same,
         "arrival_rate_per_s": rate, "throughput_requests_per_s": len(reqs) / wall,
         "eigenpairs_per_s": eig / wall, "concurrency": args.concurrency,
         "peak_running": state["peak_running"], "peak_in_flight_bytes": state["peak_in_flight_bytes"],
