@@ -42,9 +42,10 @@ UNIT = "eigenpairs/s"
 WORK_PROFILE = {"anderson3d_c_64": {"iterations": 30, "degree_width": 22.1e6, "eigenpairs": 99}}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 complex
-# Clenshaw step on this workload (ncu, see profiles/); None until captured for
-# the current kernel.
-CLENSHAW_TRAFFIC_BYTES = None
+# Clenshaw step on this workload at full width (p = 160, both V and Y terms),
+# mean of three launches of one ncu capture of the current kernel
+# (profiles/clenshaw_sell_traffic_anderson3d_c_64.md).
+CLENSHAW_TRAFFIC_BYTES = 1.3492e9
 
 
 def parse():
@@ -61,7 +62,11 @@ def parse():
     ap.add_argument("--filter-only", type=int, default=0,
                     help="time only N applications of the filter kernel (degree --degree) instead of solves")
     ap.add_argument("--degree", type=int, default=20)
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="filter-only: pin the step kernel (0 autotune, 1 SELL, 2 SELL two-step, 3 CSR)")
     ap.add_argument("--requests", type=int, default=24, help="serving workload: number of requests")
+    ap.add_argument("--compare-single", action="store_true",
+                    help="slice workloads: also solve the slices one after another")
     ap.add_argument("--concurrency", type=int, default=4, help="serving workload: worker slots")
     return ap.parse_args()
 
@@ -434,6 +439,157 @@ def serving_arm(args, dist):
                    "p": "estimated (Sec. 3.4)", "precision": "f32_defect"}}), flush=True)
 
 
+def slices_arm(args, dist):
+    """A spectrum-slice workload (synth.workloads.SLICE_WORKLOADS) through
+    apf_solve_slices: every slice's filter in one launch per Clenshaw step.
+    A step is one whole batched solve; with --compare-single the same slices
+    are also solved one after another with apf_solve."""
+    import numpy as np
+    import torch
+    from paper_2604_00914_gb300 import binding as B
+    from synth import workloads
+
+    torch.cuda.set_device(dist.local)
+    stream = torch.cuda.current_stream()
+    w = workloads.SLICE_WORKLOADS[args.workload]()
+    A = w.matrix()
+    ctx = B.Context(dist.local, stream=stream.cuda_stream)
+    M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
+    prec = {"f64": B.APF_FILTER_F64, "f32": B.APF_FILTER_F32, "f32_defect": B.APF_FILTER_F32_DEFECT}[args.precision]
+    prm = B.default_params(seed=w.seed + 1000 * dist.rank, filter_precision=prec, max_iter=args.max_iter)
+    peak, peak_kind = measured_peaks()
+
+    def one():
+        r = B.solve_slices(ctx, M, w.a, w.b, w.p, prm, allow_no_convergence=True)
+        out = (r.status, r.count(), r.slice_counts(len(w.a)), r.stats())
+        r.close()
+        return out
+
+    for _ in range(args.warmup):
+        one()
+    sampler = ClockSampler(dist.local)
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.launch_count()
+    ev0.record(stream)
+    eig, fbytes, fms, flaunch, statuses, counts, st = 0, 0.0, 0.0, 0, [], None, None
+    for _ in range(args.steps):
+        status, e, counts, st = one()
+        statuses.append(status)
+        eig += e
+        fbytes += st["filter_bytes"]
+        fms += st["filter_kernel_ms"]
+        flaunch += st["filter_launches"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop()
+    launches = ctx.launch_count() - launches0
+    ms = dist.max(ev0.elapsed_time(ev1))
+    value = dist.sum(eig) / (ms / 1e3)
+    single = None
+    if args.compare_single:
+        t0 = time.perf_counter()
+        e_single = 0
+        for s in range(len(w.a)):
+            p_s = int(w.p[s])
+            r = B.solve(ctx, M, B.default_params(a=w.a[s], b=w.b[s], p=p_s, seed=prm.seed, filter_precision=prec,
+                                                 max_iter=args.max_iter), allow_no_convergence=True)
+            e_single += r.count()
+            r.close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        single = {"value": e_single / dt, "unit": UNIT, "seconds": dt, "eigenpairs": e_single}
+    achieved = fbytes / (fms * 1e-3) / 1e9 if fms > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "f32_defect": "f32+f64"}[args.precision],
+        "data": "synthetic", "mode": "slices",
+        "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "slices": len(w.a),
+                   "intervals": [[x, y] for x, y in zip(w.a, w.b)], "p": "estimated (Sec. 3.4)",
+                   "p_total": st["p_used"], "count_estimate": st["trace_estimate"],
+                   "slice_counts": [int(c) for c in counts], "status": statuses,
+                   "iterations": st["iterations"], "max_residual": st["max_residual"],
+                   "precision": args.precision, "parallelism": f"replicas{args.gpus}"},
+        "roofline": {"kernel": "Clenshaw filter step (FP32 real, all slices per launch)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "avg_launch_us": 1e3 * fms / flaunch if flaunch else None, "launches": flaunch},
+        "single_solves": single,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    M.close()
+    ctx.close()
+
+
+def sweep_arm(args, dist):
+    """Parameter sensitivity of Sec. 4 on a synthetic matrix: the damping
+    exponent m in [0, 3] (step 0.1), the adaptive threshold tau_a in
+    [1e-4, 0.5], and C_r = C / (alpha - beta) over 13 values spanning a factor
+    12 (the paper's [10, 120] span) around the default C = 1.4 of this
+    interval, with the adaptive filter and with the fixed degree
+    k = ceil(2.5 k^(1)).  Each point is one solve; the line reports
+    iterations, mean degree, SpMV columns and time per point.  Rank 0 only."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2604_00914_gb300 import binding as B
+    from synth import matrices
+
+    if dist.rank != 0:
+        return
+    torch.cuda.set_device(dist.local)
+    A = matrices.anderson(24, 3, 4.0, SWEEP_SEED, complex_phases=True)
+    a, b = -0.012, 0.012
+    ctx = B.Context(dist.local)
+    M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
+    base = dict(a=a, b=b, p=0, seed=SWEEP_SEED, filter_precision=B.APF_FILTER_F32_DEFECT, max_iter=args.max_iter)
+
+    def run(**kw):
+        prm = B.default_params(**{**base, **kw})
+        r = B.solve(ctx, M, prm, allow_no_convergence=True)
+        st = r.stats()
+        out = {"status": r.status, "e": r.count(), "iterations": st["iterations"],
+               "avg_degree": round(st["avg_degree"], 1), "spmv_columns": st["spmv_columns"],
+               "ms": round(st["ms_total"], 1), "k1": st["k1"], "k_max": st["k_max"]}
+        r.close()
+        return out
+
+    ref = run()  # warm-up and the default point
+    st = B.default_params(**base)
+    r = B.solve(ctx, M, st, allow_no_convergence=True)
+    s = r.stats()
+    r.close()
+    l1 = 2.0 / (s["lambda_max"] - s["lambda_min"])
+    l2 = -(s["lambda_max"] + s["lambda_min"]) / (s["lambda_max"] - s["lambda_min"])
+    width = math.acos(l1 * a + l2) - math.acos(l1 * b + l2)  # alpha - beta
+    out = {"mode": "sweep", "data": "synthetic",
+           "config": {"workload": "anderson3d_c_24 sweep", "n": A.n, "interval": [a, b], "p": "estimated",
+                      "precision": "f32_defect"},
+           "default": ref, "m": [], "tau_a": [], "C_r_adaptive": [], "C_r_fixed": []}
+    for m in np.round(np.arange(0.0, 3.0001, 0.1), 1):
+        out["m"].append({"m": float(m), **run(m_d=float(m))})
+    for ta in [1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1, 0.5]:
+        out["tau_a"].append({"tau_a": ta, **run(tau_a=ta)})
+    cr0 = 1.4 / width
+    for cr in cr0 * np.linspace(0.3, 3.6, 13):
+        C = float(cr) * width
+        k1 = int(math.ceil(cr)) - 1
+        out["C_r_adaptive"].append({"C_r": float(cr), **run(C=C)})
+        out["C_r_fixed"].append({"C_r": float(cr), **run(k_fixed=int(math.ceil(2.5 * k1)))})
+    print(json.dumps(out), flush=True)
+    M.close()
+    ctx.close()
+
+
+SWEEP_SEED = 20260407
+
 # seed of the serving workload's arrival times
 BASE_ARRIVALS = 20260406
 
@@ -445,6 +601,7 @@ def filter_only(args, dist, B, ctx, M, A, w, peak, peak_kind):
     import torch
     from synth import rng
     n, p = A.n, w.p
+    M.set_filter_kernel(args.kernel)
     X = torch.from_numpy(rng.uniform_block(w.seed, rng.STREAM_INIT_BLOCK, n, p, A.is_complex)).cuda()
     Y = torch.empty_like(X)
     coef = np.linspace(1.0, 0.1, args.degree + 1)
@@ -469,6 +626,10 @@ def main():
             reference_arm(args, dist)
         elif args.workload == "serving":
             serving_arm(args, dist)
+        elif args.workload.endswith("_slices"):
+            slices_arm(args, dist)
+        elif args.workload == "sweep":
+            sweep_arm(args, dist)
         else:
             ours_arm(args, dist)
     finally:

@@ -11,6 +11,8 @@ import json
 import os
 from dataclasses import dataclass
 
+import numpy as np
+
 from . import matrices
 
 BASE_SEED = 20260401
@@ -97,10 +99,47 @@ def anderson3d_c_48() -> Workload:
 
 _BUILDERS["anderson3d_c_48"] = lambda seed: matrices.anderson(48, 3, 4.0, seed, complex_phases=True)
 
+@dataclass
+class SliceWorkload:
+    """Several disjoint intervals of one matrix (spectrum slicing)."""
+    name: str
+    seed: int
+    a: list
+    b: list
+    p: list          # 0 = estimated (Sec. 3.4)
+    is_complex: bool
+    description: str
+
+    def matrix(self) -> matrices.CSR:
+        return _BUILDERS[self.name](self.seed)
+
+
+def anderson3d_r_48_slices() -> SliceWorkload:
+    """Real 3D Anderson model, 48^3 periodic (n = 110,592), on-site disorder
+    U[-3, 3]; eight contiguous slices of equal width around E = 0 holding about
+    30 eigenvalues each (window from the oracle's count estimate, stored in
+    tests/golden); subspace sizes estimated (p = 0)."""
+    path = os.path.join(_GOLDEN, "slices_anderson3d_r_48.json")
+    with open(path) as f:
+        d = json.load(f)
+    n = len(d["a"])
+    # neighbouring slices share an end: move each slice's upper end one ulp down
+    # so that the slices are disjoint
+    b = [float(np.nextafter(x, -np.inf)) for x in d["b"]]
+    return SliceWorkload("anderson3d_r_48_slices", BASE_SEED + 12, list(d["a"]), b, [0] * n, False,
+                         "3D Anderson 48^3 periodic, W=6, real, 8 slices around E=0, p estimated")
+
+
+_BUILDERS["anderson3d_r_48_slices"] = lambda seed: matrices.anderson(48, 3, 6.0, seed, complex_phases=False)
+
 WORKLOADS = {
     "lap2d_32": lap2d_32,
     "anderson3d_c_64": anderson3d_c_64,
     "anderson3d_c_48": anderson3d_c_48,
+}
+
+SLICE_WORKLOADS = {
+    "anderson3d_r_48_slices": anderson3d_r_48_slices,
 }
 
 

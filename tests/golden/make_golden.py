@@ -7,6 +7,12 @@ Run from the repository root:  python tests/golden/make_golden.py
   the gaps around a run of 14-18 eigenvalues near the spectrum midpoint,
   taking the run whose two bounding gaps are widest; plus the eigenvalues
   inside it.
+* slices_anderson3d_r_48.json -- eight contiguous spectrum slices around
+  E = 0 of the real 48^3 Anderson model (W = 6): the half-width w of the
+  window [-w, w] holding about 240 eigenvalues, from the oracle's count
+  estimate (oracle.trace: Hutchinson trace of a degree-4000 step filter over
+  16 +-1 probes, bounds from the Gershgorin interval), cut into eight slices
+  of equal width; and the estimated count of each slice.
 """
 from __future__ import annotations
 
@@ -19,8 +25,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, ROOT)
 
-from oracle import dense  # noqa: E402
-from synth import matrices  # noqa: E402
+from oracle import chebyshev as cb  # noqa: E402
+from oracle import dense, fsi, trace  # noqa: E402
+from synth import matrices, rng  # noqa: E402
 from synth.workloads import BASE_SEED  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -49,5 +56,33 @@ def lap2d_interval():
     print("lap2d_32:", a, b, hi - lo, "min gap", best[0])
 
 
+def _count(A, lo, hi, l1, l2, Z, k):
+    coef = cb.filter_coefficients(l1 * lo + l2, l1 * hi + l2, k, cb.DAMP_LANCZOS_M, 0.5)
+    return trace.trace_estimate(A, coef, l1, l2, Z)
+
+
+def slices_anderson48(target=240, nslices=8, k=4000, probes=16):
+    seed = BASE_SEED + 12
+    A = matrices.anderson(48, 3, 6.0, seed, complex_phases=False).to_scipy()
+    lmin, lmax = fsi.gershgorin(A)
+    l1, l2 = cb.linear_map(lmin, lmax)
+    Z = rng.rademacher_block(seed, rng.STREAM_TEST, A.shape[0], probes)
+    # density at E = 0 from a window, then the half-width for `target` states
+    w0 = 0.01
+    c0 = _count(A, -w0, w0, l1, l2, Z, k)
+    w = w0 * target / max(c0, 1.0)
+    edges = np.linspace(-w, w, nslices + 1)
+    counts = [_count(A, edges[i], edges[i + 1], l1, l2, Z, k) for i in range(nslices)]
+    out = dict(a=[float(x) for x in edges[:-1]], b=[float(x) for x in edges[1:]], half_width=float(w),
+               count_estimates=[float(c) for c in counts], window_estimate_at_0_01=float(c0),
+               source=("oracle.trace.trace_estimate (degree %d, %d probes of stream %d) on "
+                       "synth.matrices.anderson(48, 3, 6.0, %d, False); Gershgorin bounds" %
+                       (k, probes, rng.STREAM_TEST, seed)))
+    with open(os.path.join(HERE, "slices_anderson3d_r_48.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print("anderson3d_r_48 slices: w", w, "counts", [round(c, 1) for c in counts])
+
+
 if __name__ == "__main__":
     lap2d_interval()
+    slices_anderson48()
