@@ -101,6 +101,7 @@ typedef struct {
   int32_t max_degree_cap;   /* safety cap on the maximum degree k, 100000 */
   double mu;                /* p = ceil(mu e~) when p = 0 (Sec. 3.4), 1.8 */
   int32_t trace_probes;     /* probe vectors m of the count estimate e~, 32 */
+  int32_t filter_graphs;    /* 1: replay recurring filter applications as CUDA graphs (default); 0: plain launches */
 } apf_params;
 
 /* Statistics of one solve (the metrics of Table 2 plus per-stage times). */

@@ -53,7 +53,7 @@ class apf_params(C.Structure):
         ("filter_precision", C.c_int32), ("spurious_rule", C.c_int32),
         ("seed", C.c_uint64), ("init_block", C.c_void_p),
         ("init_on_device", C.c_int32), ("max_degree_cap", C.c_int32),
-        ("mu", C.c_double), ("trace_probes", C.c_int32),
+        ("mu", C.c_double), ("trace_probes", C.c_int32), ("filter_graphs", C.c_int32),
     ]
 
 

@@ -115,6 +115,7 @@ void apf_params_default(apf_params* p) {
   p->max_degree_cap = 100000;
   p->mu = 1.8;
   p->trace_probes = 32;
+  p->filter_graphs = 1;
 }
 
 }  // extern "C"

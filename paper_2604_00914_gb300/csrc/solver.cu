@@ -542,6 +542,23 @@ struct FilterState {
   DBuf F, rho;                   // defect coefficients
   DBuf segs;                     // two-step pass counters
   unsigned pass = 0;
+  // CUDA graphs of the recurrence: one per (form, degree, width, input,
+  // kernel), captured the second time that application recurs and replayed
+  // afterwards.  The plain form's coefficients are the same for a given degree
+  // and the defect form's are device arrays, so a replay does the same work
+  // as the launches it replaces.  Not used with the two-step kernel (its
+  // pass counters change from launch to launch).
+  struct GraphEntry {
+    int form = 0, k = 0, kind = 0, G = 0, VPT = 0, seen = 0;
+    int64_t p = 0;
+    const void* in = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void* out = nullptr;
+    FilterCount fc;
+    int64_t launches = 0;
+  };
+  std::vector<GraphEntry> graphs;
+  bool graphs_on = false;
   std::vector<double> a;         // host a_j
   int precision = APF_FILTER_F64;
   int kmax = 0;
@@ -586,6 +603,68 @@ struct FilterState {
       }
       rho.alloc((size_t)ld * sizeof(double), ctx->stream, true);
     }
+  }
+
+  ~FilterState() {
+    for (auto& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+  }
+
+  // Run body(ev0, ev1, fc) (the launches of one recurrence; returns its output
+  // buffer) directly or through a cached graph.
+  template <class S, class Body>
+  S* run_recurrence(int form, int k, int64_t p, const void* in, const Stepper<S>& st, cudaEvent_t ev0,
+                    cudaEvent_t ev1, FilterCount* fc, Body&& body) {
+    if (!graphs_on || st.pairs()) return body(ev0, ev1, fc);
+    GraphEntry* g = nullptr;
+    for (auto& e : graphs)
+      if (e.form == form && e.k == k && e.p == p && e.in == in && e.kind == st.kind && e.G == st.G &&
+          e.VPT == st.VPT)
+        g = &e;
+    if (g == nullptr) {
+      GraphEntry e;
+      e.form = form; e.k = k; e.p = p; e.in = in; e.kind = st.kind; e.G = st.G; e.VPT = st.VPT;
+      graphs.push_back(e);
+      g = &graphs.back();
+    }
+    if (g->exec == nullptr && ++g->seen < 2) return body(ev0, ev1, fc);  // first time: run it directly
+    if (g->exec == nullptr) {
+      if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();  // e.g. the legacy default stream: no capture, no graphs
+        graphs_on = false;
+        return body(ev0, ev1, fc);
+      }
+      FilterCount local;
+      const int64_t l0 = ctx->launches;
+      S* out = nullptr;
+      try {
+        out = body(nullptr, nullptr, &local);
+      } catch (...) {
+        cudaGraph_t gr = nullptr;
+        cudaStreamEndCapture(ctx->stream, &gr);
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        throw;
+      }
+      cudaGraph_t gr = nullptr;
+      APF_CUDA(cudaStreamEndCapture(ctx->stream, &gr));
+      const cudaError_t ie = cudaGraphInstantiate(&g->exec, gr, 0);
+      cudaGraphDestroy(gr);
+      APF_CUDA(ie);
+      g->out = out;
+      g->fc = local;
+      g->launches = ctx->launches - l0;
+      ctx->launches = l0;  // counted again below, at the replay
+    }
+    if (ev0) APF_CUDA(cudaEventRecord(ev0, ctx->stream));
+    APF_CUDA(cudaGraphLaunch(g->exec, ctx->stream));
+    if (ev1) APF_CUDA(cudaEventRecord(ev1, ctx->stream));
+    ctx->launches += g->launches;
+    fc->launches += g->fc.launches;
+    fc->steps += g->fc.steps;
+    fc->bytes += g->fc.bytes;
+    fc->step_bytes += g->fc.step_bytes;
+    return static_cast<S*>(g->out);
   }
 
   // counters for the smallest tile (8 rows): ceil(n / 8 / 32) segments
@@ -633,8 +712,10 @@ struct FilterState {
     APF_REQUIRE(k <= kmax, APF_ERR_ARG);
     const int64_t nnz = A->nnz;
     if (precision == APF_FILTER_F64) {
-      T* out = clenshaw_plain<T>(ctx, stepper64(), n, nnz, V, ld, p, a.data(), k, B1.as<T>(),
-                                 B2.as<T>(), ev0, ev1, fc);
+      const Stepper<T> s64 = stepper64();
+      T* out = run_recurrence<T>(0, k, p, V, s64, ev0, ev1, fc, [&](cudaEvent_t e0, cudaEvent_t e1, FilterCount* f) {
+        return clenshaw_plain<T>(ctx, s64, n, nnz, V, ld, p, a.data(), k, B1.as<T>(), B2.as<T>(), e0, e1, f);
+      });
       copy_block<T>(ctx, n, p, out, ld, X, ld);
       return;
     }
@@ -645,14 +726,18 @@ struct FilterState {
       DBuf scratch((size_t)p * sizeof(double), ctx->stream, false);
       residual_norms<T>(ctx, n, p, AV, V, ld, lam, scratch.as<double>(), Y32.as<TL>(), l1, rows_out(st));
       defect_coefficients(ctx, p, ld, k, coef_dev.as<double>(), lam, l1, l2, F.as<float>(), rho.as<double>());
-      TL* D = clenshaw_defect<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, p, F.as<float>(), k, B1.as<TL>(),
-                                  B2.as<TL>(), ev0, ev1, fc);
+      TL* D = run_recurrence<TL>(1, k, p, Y32.p, st, ev0, ev1, fc, [&](cudaEvent_t e0, cudaEvent_t e1, FilterCount* f) {
+        return clenshaw_defect<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, p, F.as<float>(), k, B1.as<TL>(),
+                                   B2.as<TL>(), e0, e1, f);
+      });
       defect_combine<T>(ctx, n, p, V, ld, rho.as<double>(), D, ld, X, ld, rows_out(st));
       return;
     }
     cast_block_rows<T, TL>(ctx, n, p, V, ld, Y32.as<TL>(), ld, rows_in(st));
-    TL* out = clenshaw_plain<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, p, a.data(), k, B1.as<TL>(),
-                                 B2.as<TL>(), ev0, ev1, fc);
+    TL* out = run_recurrence<TL>(2, k, p, Y32.p, st, ev0, ev1, fc, [&](cudaEvent_t e0, cudaEvent_t e1, FilterCount* f) {
+      return clenshaw_plain<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, p, a.data(), k, B1.as<TL>(), B2.as<TL>(), e0,
+                                e1, f);
+    });
     cast_block_rows<TL, T>(ctx, n, p, out, ld, X, ld, rows_out(st));
   }
 
@@ -1164,6 +1249,7 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
   st.norm_a = bd.normA;
   FilterState<T> fs;
   fs.init(ctx, A, S.ld, bd.l1, bd.l2, S.coef, prm->filter_precision);
+  fs.graphs_on = prm->filter_graphs != 0;
   APF_CUDA(cudaStreamSynchronize(ctx->stream));
   st.ms_setup = std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
 

@@ -212,3 +212,21 @@ def test_matrix_without_stored_diagonal(B, ctx):
     a, b = _interval_around(lam, 1.1, 6)
     out = _solve(B, ctx, A2, a, b, 20, 4)
     _check(out, A2, lam[(lam >= a) & (lam <= b)])
+
+
+@pytest.mark.parametrize("prec", ["F64", "F32", "F32_DEFECT"])
+def test_graph_replay_gives_the_same_solve(B, ctx, prec):
+    """Recurring filter applications replayed as CUDA graphs do the same work
+    as plain launches: identical eigenvalues, residuals and counters."""
+    A = matrices.anderson(9, 3, 4.0, 14, True)
+    lam = np.linalg.eigvalsh(A.to_dense())
+    a, b = _interval_around(lam, 0.4, 8)
+    kw = dict(filter_precision=_prec(B, prec), max_iter=12 if prec == "F32" else 50)
+    on = _solve(B, ctx, A, a, b, 16, 5, filter_graphs=1, **kw)
+    off = _solve(B, ctx, A, a, b, 16, 5, filter_graphs=0, **kw)
+    assert on["status"] == off["status"]
+    assert np.array_equal(on["lam"], off["lam"]) and np.array_equal(on["res"], off["res"])
+    for key in ("iterations", "filter_launches", "filter_steps", "spmv_columns", "gpu_launches"):
+        assert on["stats"][key] == off["stats"][key], key
+    if prec != "F32":
+        assert on["status"] == 0
