@@ -45,7 +45,7 @@ WORK_PROFILE = {"anderson3d_c_64": {"iterations": 30, "degree_width": 22.1e6, "e
 # Clenshaw step on this workload at full width (p = 160, both V and Y terms),
 # mean of three launches of one ncu capture of the current kernel
 # (profiles/clenshaw_sell_traffic_anderson3d_c_64.md).
-CLENSHAW_TRAFFIC_BYTES = 1.3492e9
+CLENSHAW_TRAFFIC_BYTES = 1.3486e9
 
 
 def parse():
