@@ -74,16 +74,22 @@ def parse():
 # ---- distributed plumbing ---------------------------------------------------------------
 
 class Dist:
+    """Rank bookkeeping and the two reductions the timing needs (max of the
+    ranks' times, sum of their eigenpairs).  NCCL on GPUs, gloo on the CPU."""
+
     def __init__(self):
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.on = self.world > 1
+        self.device = "cpu"
         if self.on:
             import torch
             import torch.distributed as dist
-            torch.cuda.set_device(self.local)
-            dist.init_process_group("nccl")
+            if torch.cuda.is_available():
+                torch.cuda.set_device(self.local)
+                self.device = "cuda"
+            dist.init_process_group("nccl" if self.device == "cuda" else "gloo")
             self.dist = dist
 
     def barrier(self):
@@ -94,7 +100,7 @@ class Dist:
         if not self.on:
             return x
         import torch
-        t = torch.tensor([float(x)], device="cuda", dtype=torch.float64)
+        t = torch.tensor([float(x)], device=self.device, dtype=torch.float64)
         self.dist.all_reduce(t, op=op)
         return float(t.item())
 

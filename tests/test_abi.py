@@ -86,3 +86,18 @@ def test_argument_errors_without_device(lib):
     assert lib.apf_filter_coefficients(0.3, 0.2, 9, 0, 0.5, out.ctypes.data) == binding.APF_ERR_ARG
     assert lib.apf_filter_coefficients(-1.5, 0.2, 9, 0, 0.5, out.ctypes.data) == binding.APF_ERR_ARG
     assert lib.apf_solve(None, None, None, None) == binding.APF_ERR_ARG
+    # the entry points beyond one solve reject missing handles before any device work
+    import ctypes
+    h = ctypes.c_void_p()
+    cnt = np.zeros(4, dtype=np.int64)
+    assert lib.apf_solve_slices(None, None, 1, None, None, None, None, None) == binding.APF_ERR_ARG
+    assert lib.apf_result_slice_counts(None, 1, cnt.ctypes.data) == binding.APF_ERR_ARG
+    assert lib.apf_count_estimate(None, None, None, 4, 0.1, 0.0, 0, 8, 1, None) == binding.APF_ERR_ARG
+    assert lib.apf_matrix_set_filter_kernel(None, 1, 0, 0) == binding.APF_ERR_ARG
+    assert lib.apf_server_create(None, 0, 2, 0) == binding.APF_ERR_ARG
+    assert lib.apf_server_create(ctypes.byref(h), 0, 0, 0) == binding.APF_ERR_ARG  # no worker slot
+    assert lib.apf_server_create(ctypes.byref(h), 0, 65, 0) == binding.APF_ERR_ARG
+    assert lib.apf_server_submit(None, 10, 0, None, None, None, 0, None, None) == binding.APF_ERR_ARG
+    assert lib.apf_server_wait(None, 1, ctypes.byref(h), None) == binding.APF_ERR_ARG
+    assert lib.apf_server_state(None, None) == binding.APF_ERR_ARG
+    assert lib.apf_server_destroy(None) == binding.APF_OK
