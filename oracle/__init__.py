@@ -19,6 +19,8 @@ Filtering for Hermitian Interior Eigenproblems":
   eigendecomposition, and an eigenvalue count by Sylvester inertia.
 * ``fsi`` -- Lanczos spectrum bounds (Sec. 3.4), Cholesky QR, Rayleigh-Ritz
   (Alg. 1), and the whole of Alg. 4 (AdaPolySI) step by step.
+* ``trace`` -- the eigenvalue count estimate (Hutchinson trace of the filter)
+  and the subspace size p = ceil(mu e~) of Sec. 3.4.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against
 closed forms, quadrature, brute force or the paper's theorems; see
