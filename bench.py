@@ -245,7 +245,9 @@ def ours_arm(args, dist):
     from synth import workloads
 
     torch.cuda.set_device(dist.local)
-    stream = torch.cuda.current_stream()
+    # a stream of its own (not the legacy default stream): the library launches
+    # on it and the timing events below are recorded on it
+    stream = torch.cuda.Stream()
     w = workloads.WORKLOADS[args.workload]()
     A = w.matrix()
     ctx = B.Context(dist.local, stream=stream.cuda_stream)
@@ -456,7 +458,7 @@ def slices_arm(args, dist):
     from synth import workloads
 
     torch.cuda.set_device(dist.local)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # the library's stream and the timing events' stream
     w = workloads.SLICE_WORKLOADS[args.workload]()
     A = w.matrix()
     ctx = B.Context(dist.local, stream=stream.cuda_stream)
