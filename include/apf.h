@@ -102,6 +102,7 @@ typedef struct {
   double mu;                /* p = ceil(mu e~) when p = 0 (Sec. 3.4), 1.8 */
   int32_t trace_probes;     /* probe vectors m of the count estimate e~, 32 */
   int32_t filter_graphs;    /* 1: replay recurring filter applications as CUDA graphs (default); 0: plain launches */
+  int32_t gram_tensor_cores; /* 1: Gram products of CholQR / Rayleigh-Ritz on the tensor cores (apf_gram_tc, default); 0: FP64 cores */
 } apf_params;
 
 /* Statistics of one solve (the metrics of Table 2 plus per-stage times). */
@@ -323,10 +324,23 @@ apf_status apf_spmm(apf_ctx* ctx, const apf_matrix* A, const void* X, int64_t ld
 
 /* G = X^H Y: the tall-skinny Gram product of the Cholesky QR and
  * Rayleigh-Ritz steps of Alg. 4.  X: n x pa, Y: n x pb,
- * G: pa x pb row-major (ldg >= pb), all device, of `dtype`. */
+ * G: pa x pb row-major (ldg >= pb), all device, of `dtype`.  apf_gram_tc
+ * below computes the same product on the tensor cores. */
 apf_status apf_gram(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t pb,
                     const void* X, int64_t ldx, const void* Y, int64_t ldy,
                     void* G, int64_t ldg);
+
+/* The same G = X^H Y as apf_gram, to FP64 accuracy, on the bf16 tensor cores:
+ * each column is split into 7 signed 8-bit slices under a per-column power of
+ * two (the Ozaki scheme), the slice products accumulate exactly in FP32 over
+ * 64-row chunks and are carried in FP64.  The error relative to
+ * 2^(e_a + e_b), where 2^e_a bounds column a's largest entry, is about
+ * n 2^-55: that of an FP64 product for columns whose entries are of one size.
+ * Same arguments and errors as apf_gram; pa, pb <= APF_MAX_P.  Allocates the
+ * slices (7 x 2 x n x pa bf16 for complex X) for the call. */
+apf_status apf_gram_tc(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t pb,
+                       const void* X, int64_t ldx, const void* Y, int64_t ldy,
+                       void* G, int64_t ldg);
 
 /* Orthogonalisation of Alg. 4: X (device n x p) is replaced by Q with X = Q R, by CholQR2
  * (shifted CholQR3 when the first factorisation breaks down). */

@@ -54,6 +54,7 @@ class apf_params(C.Structure):
         ("seed", C.c_uint64), ("init_block", C.c_void_p),
         ("init_on_device", C.c_int32), ("max_degree_cap", C.c_int32),
         ("mu", C.c_double), ("trace_probes", C.c_int32), ("filter_graphs", C.c_int32),
+        ("gram_tensor_cores", C.c_int32),
     ]
 
 
@@ -146,6 +147,7 @@ SIGNATURES = {
     "apf_filter_apply_defect": (_I32, [_P, _P, _P, _I32, _D, _D, _P, _P, _P, _I64, _I64, _P, _I64]),
     "apf_spmm": (_I32, [_P, _P, _P, _I64, _I64, _P, _I64]),
     "apf_gram": (_I32, [_P, _I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64]),
+    "apf_gram_tc": (_I32, [_P, _I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64]),
     "apf_cholqr2": (_I32, [_P, _I32, _I64, _I64, _P, _I64]),
     "apf_eigh_small": (_I32, [_P, _I32, _I64, _P, _I64, _P, _P, _I64]),
     "apf_rayleigh_ritz": (_I32, [_P, _P, _P, _I64, _I64, _P, _P, _I64]),
@@ -521,6 +523,16 @@ def gram(ctx, X, Y, G):
     dt = APF_C128 if X.is_complex() else APF_R64
     ctx.lib.check(ctx.lib.apf_gram(ctx.h, dt, n, pa, pb, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
                                    _ptr(G), G.stride(0)), ctx.h)
+    return G
+
+
+def gram_tc(ctx, X, Y, G):
+    """apf_gram_tc: G = X^H Y on the tensor cores (FP64-accurate slicing)."""
+    n, pa = X.shape
+    pb = Y.shape[1]
+    dt = APF_C128 if X.is_complex() else APF_R64
+    ctx.lib.check(ctx.lib.apf_gram_tc(ctx.h, dt, n, pa, pb, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
+                                      _ptr(G), G.stride(0)), ctx.h)
     return G
 
 

@@ -180,6 +180,10 @@ void gershgorin(apf_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* c
 // ---- dense tall-skinny products (k_dense.cu) ---------------------------------
 // G (pa x pb, ldg) = X^H Y; X: n x pa (ldx), Y: n x pb (ldy).  hermitian: X == Y,
 // only the upper tiles are computed and mirrored.
+// the same product on the tensor cores, FP64-accurate by bf16 slicing (k_gram_tc.cu)
+template <class T>
+void gram_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_t ldx, const T* Y, int64_t ldy,
+             T* G, int64_t ldg, bool hermitian);
 template <class T>
 void gram(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_t ldx,
           const T* Y, int64_t ldy, T* G, int64_t ldg, bool hermitian);

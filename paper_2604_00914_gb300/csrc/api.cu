@@ -116,6 +116,7 @@ void apf_params_default(apf_params* p) {
   p->mu = 1.8;
   p->trace_probes = 32;
   p->filter_graphs = 1;
+  p->gram_tensor_cores = 1;
 }
 
 }  // extern "C"
@@ -730,6 +731,23 @@ apf_status apf_gram(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t 
   else
     apf::gram<double>(ctx, n, pa, pb, static_cast<const double*>(X), ldx, static_cast<const double*>(Y), ldy,
                       static_cast<double*>(G), ldg, false);
+  APF_CUDA(cudaStreamSynchronize(ctx->stream));
+  APF_CATCH(ctx)
+}
+
+apf_status apf_gram_tc(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t pb, const void* X,
+                       int64_t ldx, const void* Y, int64_t ldy, void* G, int64_t ldg) {
+  if (!ctx || !X || !Y || !G || n < 1 || pa < 1 || pb < 1 || ldx < pa || ldy < pb || ldg < pb) return APF_ERR_ARG;
+  if (pa > APF_MAX_P || pb > APF_MAX_P) return APF_ERR_ARG;
+  if (dtype != APF_R64 && dtype != APF_C128) return APF_ERR_ARG;
+  APF_TRY(ctx)
+  bind(ctx);
+  if (dtype == APF_C128)
+    apf::gram_tc<double2>(ctx, n, pa, pb, static_cast<const double2*>(X), ldx, static_cast<const double2*>(Y), ldy,
+                          static_cast<double2*>(G), ldg, false);
+  else
+    apf::gram_tc<double>(ctx, n, pa, pb, static_cast<const double*>(X), ldx, static_cast<const double*>(Y), ldy,
+                         static_cast<double*>(G), ldg, false);
   APF_CUDA(cudaStreamSynchronize(ctx->stream));
   APF_CATCH(ctx)
 }

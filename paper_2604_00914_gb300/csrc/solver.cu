@@ -830,11 +830,19 @@ struct SmallWork {
   }
 };
 
+// The Gram product on the FP64 cores or on the tensor cores (bf16 slicing).
+template <class T>
+static void gram_on(apf_ctx* ctx, bool tc, int64_t n, int64_t pa, int64_t pb, const T* X, int64_t ldx, const T* Y,
+                    int64_t ldy, T* G, int64_t ldg, bool hermitian) {
+  if (tc) gram_tc<T>(ctx, n, pa, pb, X, ldx, Y, ldy, G, ldg, hermitian);
+  else gram<T>(ctx, n, pa, pb, X, ldx, Y, ldy, G, ldg, hermitian);
+}
+
 // One Cholesky QR pass Xout = X R^{-1}, R from G = X^H X (+ shift I).
 template <class T>
 static bool cholqr_pass(apf_ctx* ctx, int64_t n, int64_t p, const T* X, int64_t ld, T* Xout,
-                        SmallWork<T>& sw, bool shifted) {
-  gram<T>(ctx, n, p, p, X, ld, X, ld, sw.G, p, true);
+                        SmallWork<T>& sw, bool shifted, bool tc = false) {
+  gram_on<T>(ctx, tc, n, p, p, X, ld, X, ld, sw.G, p, true);
   double shift = 0.0;
   if (shifted) {
     // shifted Cholesky QR (Fukaya et al. 2020): s = 11 (n p + p (p + 1)) u ||X||_F^2
@@ -879,21 +887,21 @@ static void spmm_plain(apf_ctx* ctx, const apf_matrix* A, const T* X, int64_t ld
 template <class T>
 static void orth_rr(apf_ctx* ctx, const apf_matrix* A, int64_t p, int64_t ld, T* X, T* X1,
                     const T* Vlock, int64_t nlock, int64_t ldl, SmallWork<T>& sw, T* Vh, T* AVh,
-                    double* w, double* res) {
+                    double* w, double* res, bool tc) {
   const int64_t n = A->n;
   for (int pass = 0; pass < 2 && nlock > 0; ++pass) {
-    gram<T>(ctx, n, nlock, p, Vlock, ldl, X, ld, sw.C, p, false);
+    gram_on<T>(ctx, tc, n, nlock, p, Vlock, ldl, X, ld, sw.C, p, false);
     gemm_tall<T>(ctx, n, nlock, p, Vlock, ldl, sw.C, p, X, ld, -1.0, 1.0, X, ld, false);
   }
-  if (!cholqr_pass<T>(ctx, n, p, X, ld, X1, sw, false)) {
-    if (!cholqr_pass<T>(ctx, n, p, X, ld, X1, sw, true)) throw ApfError{APF_ERR_CHOL, "shifted CholQR"};
-    if (!cholqr_pass<T>(ctx, n, p, X1, ld, X, sw, false)) throw ApfError{APF_ERR_CHOL, "CholQR3"};
+  if (!cholqr_pass<T>(ctx, n, p, X, ld, X1, sw, false, tc)) {
+    if (!cholqr_pass<T>(ctx, n, p, X, ld, X1, sw, true, tc)) throw ApfError{APF_ERR_CHOL, "shifted CholQR"};
+    if (!cholqr_pass<T>(ctx, n, p, X1, ld, X, sw, false, tc)) throw ApfError{APF_ERR_CHOL, "CholQR3"};
     copy_block<T>(ctx, n, p, X, ld, X1, ld);
   }
   T* AX = X;  // X is dead: reuse it for A X1
   spmm_plain<T>(ctx, A, X1, ld, p, AX);
-  gram<T>(ctx, n, p, p, X1, ld, X1, ld, sw.G, p, true);
-  gram<T>(ctx, n, p, p, X1, ld, AX, ld, sw.G3, p, true);  // X1^H A X1 is Hermitian
+  gram_on<T>(ctx, tc, n, p, p, X1, ld, X1, ld, sw.G, p, true);
+  gram_on<T>(ctx, tc, n, p, p, X1, ld, AX, ld, sw.G3, p, true);  // X1^H A X1 is Hermitian
   if (!cholesky_checked<T>(ctx, p, sw.G, p, 0.0)) throw ApfError{APF_ERR_CHOL, "CholQR2 second pass"};
   tri_inv_upper<T>(ctx, p, sw.G, p, sw.Ri, p);
   small_gemm<T>(ctx, p, p, p, 'N', sw.G3, p, 'N', sw.Ri, p, sw.T1, p, 1.0, 0.0);
@@ -978,9 +986,9 @@ struct IntervalState {
   // after the filter wrote X: orthogonalisation against the locked vectors,
   // Rayleigh-Ritz and residual norms, and the copies of w and res to the host
   // (complete after the next synchronisation)
-  void orth(apf_ctx* ctx, const apf_matrix* A, SmallWork<T>& sw) {
+  void orth(apf_ctx* ctx, const apf_matrix* A, SmallWork<T>& sw, bool tc) {
     orth_rr<T>(ctx, A, pa, ld, X.as<T>(), X1.as<T>(), Vlock.as<T>(), nlock, ld, sw, Vh.as<T>(), AVh.as<T>(),
-               w, res);
+               w, res, tc);
     APF_CUDA(cudaMemcpyAsync(hw.data(), w, (size_t)pa * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     APF_CUDA(cudaMemcpyAsync(hr.data(), res, (size_t)pa * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   }
@@ -1273,7 +1281,7 @@ static void solve_t(apf_ctx* ctx, const apf_matrix* A, const apf_params* prm, ap
     ++iters;
     APF_CUDA(cudaEventRecord(ev.e1, ctx->stream));
     // orthogonalisation, Rayleigh-Ritz, residuals
-    S.orth(ctx, A, sw);
+    S.orth(ctx, A, sw, prm->gram_tensor_cores != 0);
     APF_CUDA(cudaEventRecord(ev.e2, ctx->stream));
     check_device_after_rr(ctx);
     S.check(ctx, A, prm, bd.l1, bd.l2, bd.normA);
@@ -1430,7 +1438,7 @@ static void solve_slices_t(apf_ctx* ctx, const apf_matrix* A, int ns, const doub
     deg_sum += kc[0];
     ++iters;
     APF_CUDA(cudaEventRecord(ev.e1, ctx->stream));
-    for (int s : act) S[(size_t)s].orth(ctx, A, sw);
+    for (int s : act) S[(size_t)s].orth(ctx, A, sw, prm->gram_tensor_cores != 0);
     APF_CUDA(cudaEventRecord(ev.e2, ctx->stream));
     check_device_after_rr(ctx);
     std::vector<double> row = {(double)kc[0], 0.0, 0.0, 0.0, 0.0, 0.0};

@@ -53,7 +53,7 @@ def test_struct_sizes_match_header(lib):
     assert p.C == 1.4 and p.k_ratio == 2.5 and p.m_d == 0.5 and p.tau_a == 1e-3 and p.tau_c == 1e-10
     assert p.max_iter == 50 and p.lanczos_steps == 40 and p.spurious_rule == 1
     assert p.max_degree_cap == 100000 and p.init_block is None
-    assert p.mu == 1.8 and p.trace_probes == 32 and p.filter_graphs == 1
+    assert p.mu == 1.8 and p.trace_probes == 32 and p.filter_graphs == 1 and p.gram_tensor_cores == 1
 
 
 def test_host_entry_points_without_gpu(lib):
