@@ -333,9 +333,10 @@ apf_status apf_gram(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t 
 /* The same G = X^H Y as apf_gram, to FP64 accuracy, on the bf16 tensor cores:
  * each column is split into 7 signed 8-bit slices under a per-column power of
  * two (the Ozaki scheme), the slice products accumulate exactly in FP32 over
- * 64-row chunks and are carried in FP64.  The error relative to
- * 2^(e_a + e_b), where 2^e_a bounds column a's largest entry, is about
- * n 2^-55: that of an FP64 product for columns whose entries are of one size.
+ * 64-row chunks and are carried in FP64.  The error is at most about
+ * n 2^(e_a + e_b - 53), where 2^e_a (< twice column a's largest entry)
+ * bounds column a: within a small factor of an FP64 product's worst case
+ * for columns whose entries are of one size.
  * Same arguments and errors as apf_gram; pa, pb <= APF_MAX_P.  Allocates the
  * slices (7 x 2 x n x pa bf16 for complex X) for the call. */
 apf_status apf_gram_tc(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t pb,

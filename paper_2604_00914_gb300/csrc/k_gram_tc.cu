@@ -6,11 +6,13 @@
 //
 // Column a of X gets the exponent e_a with |x_ia| < 2^e_a (real and imaginary
 // parts alike).  Each part is cut into S = 7 signed integer slices of at most
-// 8 bits:  x_ia = 2^(e_a - 7) sum_s sigma_s 2^(-8 s) (up to 2^(e_a - 62)),
-// sigma_s in [-128, 128], stored as bf16 (exact).  Then
+// 8 bits:  x_ia = 2^(e_a - 7) sum_s sigma_s 2^(-8 s) + r_ia, |r_ia| <= 2^(e_a - 56)
+// (55 bits below 2^e_a: exact for entries within a factor 4 of the column's
+// largest), sigma_s in [-128, 128], stored as bf16 (exact).  Then
 //   sum_i x_ia y_ib = 2^(e_a + e_b - 14) sum_d 2^(-8 d) sum_{s + t = d} P_st,
-// P_st = sum_i sigma_s(x_ia) sigma_t(y_ib), keeping d <= S - 1 (the dropped
-// terms are below 2^-55 relative to 2^(e_a + e_b) per row).  The P_st are sums
+// P_st = sum_i sigma_s(x_ia) sigma_t(y_ib), keeping d <= S - 1: with the
+// remainders, the dropped terms are at most about 2^(e_a + e_b - 53) per row
+// (worst case; random signs make the sum far smaller).  The P_st are sums
 // of products of integers below 2^14: with d + 1 <= 7 slice pairs, the real
 // and imaginary combinations (two products each) and 64 rows per chunk, every
 // partial sum stays below 896 * 2^14 < 2^24, so the tensor cores' FP32

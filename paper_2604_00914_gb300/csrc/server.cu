@@ -69,15 +69,18 @@ namespace {
 // Device bytes of one solve, estimated from the sizes: the matrix in CSR
 // (FP64 values), its FP32 scaled copy and SELL-8 copies (padding allowance
 // included), five n x p blocks of the subspace state, three FP32 recurrence
-// blocks, the result and its residual check, and 64 MiB of small buffers.
-// p = 0 (estimated size) counts as min(n, 256).
-int64_t footprint(int64_t n, int64_t nnz, int32_t dtype, int64_t p) {
+// blocks, the result and its residual check, the bf16 slices of two operands
+// of a tensor-core Gram product when those are on (7 slices per real part),
+// and 64 MiB of small buffers.  p = 0 (estimated size) counts as min(n, 256).
+int64_t footprint(int64_t n, int64_t nnz, int32_t dtype, int64_t p, bool gram_tc) {
   const int64_t s = dtype == APF_C128 ? 16 : 8, sl = s / 2;
+  const int64_t parts = dtype == APF_C128 ? 2 : 1;
   const int64_t pp = p > 0 ? p : std::min<int64_t>(n, 256);
   const int64_t ld = apf::round_up(pp, 8);
   const int64_t mat = nnz * (s + 4) + (n + 1) * 8 + 4 * nnz * (sl + 8);
   const int64_t blocks = 8 * n * ld * s + 3 * n * ld * sl;
-  return mat + blocks + (64ll << 20);
+  const int64_t slices = gram_tc ? 2 * 7 * parts * apf::round_up(n, 64) * apf::round_up(pp, 32) * 2 : 0;
+  return mat + blocks + slices + (64ll << 20);
 }
 
 bool admissible(const apf_server* s, const Request* r) {
@@ -198,7 +201,7 @@ apf_status apf_server_submit(apf_server* s, int64_t n, int64_t nnz, const int64_
   r->nnz = nnz;
   r->dtype = dtype;
   r->prm = *params;
-  r->footprint = footprint(n, nnz, dtype, params->p);
+  r->footprint = footprint(n, nnz, dtype, params->p, params->gram_tensor_cores != 0);
   if (r->footprint > s->budget) return APF_ERR_OOM;
   const size_t vs = dtype == APF_C128 ? 16 : 8;
   r->rowptr.assign(rowptr, rowptr + n + 1);
