@@ -286,9 +286,16 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
   }
   APF_REQUIRE(!cands.empty(), APF_ERR_ARG);
   const bool verbose = getenv("APF_VERBOSE") != nullptr;
-  cudaEvent_t e0, e1;
-  APF_CUDA(cudaEventCreate(&e0));
-  APF_CUDA(cudaEventCreate(&e1));
+  struct EventPair {  // destroyed on every exit, including a failed launch
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  APF_CUDA(cudaEventCreate(&ev.a));
+  APF_CUDA(cudaEventCreate(&ev.b));
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   float best = 1e30f;
   Cand pick = cands[0];
   for (const Cand& c : cands) {
@@ -319,8 +326,6 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
     if (ms < best) { best = ms; pick = c; }
   }
   if (fetch_device_error(st.ctx) != 0) throw ApfError{APF_ERR_TIMEOUT, "filter tuning"};
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   st.kind = pick.kind;
   st.G = pick.G;
   st.VPT = pick.VPT;
