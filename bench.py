@@ -41,11 +41,10 @@ UNIT = "eigenpairs/s"
 # which runs without a GPU; the main arm uses the profile of its own solves.
 WORK_PROFILE = {"anderson3d_c_64": {"iterations": 30, "degree_width": 22.1e6, "eigenpairs": 99}}
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 complex
-# Clenshaw step on this workload at full width (p = 160, both V and Y terms),
-# mean of three launches of one ncu capture of the current kernel
-# (profiles/clenshaw_sell_traffic_anderson3d_c_64.md).
-CLENSHAW_TRAFFIC_BYTES = 1.3486e9
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32
+# Clenshaw step at full width (both V and Y terms), mean of three launches of
+# one ncu capture of the kernel (profiles/clenshaw_sell_traffic_<workload>.md).
+TRAFFIC_BYTES = {"anderson3d_c_64": 1.3486e9}
 
 
 def parse():
@@ -58,6 +57,12 @@ def parse():
     ap.add_argument("--precision", default="f32_defect", choices=["f64", "f32", "f32_defect"])
     ap.add_argument("--max-iter", type=int, default=60)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1,
+                    help="end-to-end solves through the C ABI from host buffers (after the timed ones)")
+    ap.add_argument("--p", type=int, default=-1, help="subspace size override (0: estimated, Sec. 3.4)")
+    ap.add_argument("--f64-compare", default="anderson3d_c_40",
+                    help="workload on which one plain FP64 solve is timed against the FP32 defect form "
+                         "('' to skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--filter-only", type=int, default=0,
                     help="time only N applications of the filter kernel (degree --degree) instead of solves")
@@ -253,7 +258,8 @@ def ours_arm(args, dist):
     ctx = B.Context(dist.local, stream=stream.cuda_stream)
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
     prec = {"f64": B.APF_FILTER_F64, "f32": B.APF_FILTER_F32, "f32_defect": B.APF_FILTER_F32_DEFECT}[args.precision]
-    prm = B.default_params(a=w.a, b=w.b, p=w.p, seed=w.seed + 1000 * dist.rank, filter_precision=prec,
+    p_used = w.p if args.p < 0 else args.p
+    prm = B.default_params(a=w.a, b=w.b, p=p_used, seed=w.seed + 1000 * dist.rank, filter_precision=prec,
                            max_iter=args.max_iter)
     peak, peak_kind = measured_peaks()
 
@@ -281,8 +287,11 @@ def ours_arm(args, dist):
     deg_width = 0.0
     iters = 0
     maxres = 0.0
+    p_stat = deg_seq = None
     for _ in range(args.steps):
         e, st, hist = one_solve()
+        p_stat = st["p_used"]
+        deg_seq = [int(h["degree"]) for h in hist]
         eig += e
         fbytes += st["filter_bytes"]
         fstep_bytes += st["filter_step_bytes"]
@@ -304,7 +313,7 @@ def ours_arm(args, dist):
 
     # end to end through the C ABI: host CSR in pinned memory -> solve -> eigenpairs to host
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.e2e_steps > 0:
         rp = torch.from_numpy(A.rowptr).pin_memory()
         ci = torch.from_numpy(A.colidx).pin_memory()
         vv = torch.from_numpy(A.vals).pin_memory()
@@ -314,7 +323,7 @@ def ours_arm(args, dist):
         t0 = time.perf_counter()
         e_tot = 0
         d2h = 0
-        for _ in range(args.steps):
+        for _ in range(args.e2e_steps):
             M2 = B.Matrix.from_csr(ctx, A.n, rp.numpy(), ci.numpy(), vv.numpy())
             r = B.solve(ctx, M2, prm)
             e = r.count()
@@ -328,7 +337,11 @@ def ours_arm(args, dist):
         torch.cuda.synchronize()
         dt = dist.max(time.perf_counter() - t0)
         e2e = {"value": dist.sum(e_tot) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+               "d2h_bytes_per_step": int(d2h), "solves": args.e2e_steps}
+
+    plain = None
+    if args.f64_compare and dist.rank == 0:
+        plain = f64_compare(args, dist, B, stream)
 
     cpu = None
     if dist.rank == 0 and args.gpus == 1 and not args.no_cpu_baseline:
@@ -340,26 +353,34 @@ def ours_arm(args, dist):
 
     achieved = fbytes / (fms * 1e-3) / 1e9 if fms > 0 else None
     per_step = fstep_bytes / (fms * 1e-3) / 1e9 if fms > 0 else None
+    kind = "complex" if A.is_complex else "real"
+    bits = {"f64": "FP64", "f32": "FP32", "f32_defect": "FP32"}[args.precision]
+    blk_mb = A.n * w.p * (8 if A.is_complex else 4) / 1e6
+    traffic = TRAFFIC_BYTES.get(args.workload) if args.precision != "f64" and args.p < 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f64": "c128", "f32": "c64", "f32_defect": "c64+c128"}[args.precision],
+        "dtype": (({"f64": "c128", "f32": "c64", "f32_defect": "c64+c128"} if A.is_complex else
+                   {"f64": "f64", "f32": "f32", "f32_defect": "f32+f64"})[args.precision]),
         "data": "synthetic",
-        "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "p": w.p, "interval": [w.a, w.b],
+        "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "p": p_used, "interval": [w.a, w.b],
                    "precision": args.precision, "eigenpairs_per_solve": eig / args.steps,
                    "iterations_per_solve": iters / args.steps, "max_residual": maxres,
-                   "l2": "inputs larger than L2 (blocks 335-671 MB)", "parallelism": f"replicas{args.gpus}"},
-        "roofline": {"kernel": "Clenshaw filter step (FP32 complex, SELL-8)", "bound": "hbm",
+                   "p_used": p_stat, "degree_sequence": deg_seq,
+                   "l2": f"inputs larger than L2 (FP32 block {blk_mb:.0f} MB, FP64 block {2 * blk_mb:.0f} MB)",
+                   "parallelism": f"replicas{args.gpus}"},
+        "roofline": {"kernel": f"Clenshaw filter step ({bits} {kind}, SELL-8)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,
-                     "traffic": CLENSHAW_TRAFFIC_BYTES,
+                     "traffic": traffic,
                      "avg_launch_us": 1e3 * fms / flaunch if flaunch else None,
                      "launches": flaunch, "steps": fsteps,
                      "us_per_step": 1e3 * fms / fsteps if fsteps else None,
                      "one_step_equivalent_gbs": per_step},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "plain_f64": plain,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -367,6 +388,60 @@ def ours_arm(args, dist):
         print(json.dumps(line), flush=True)
     M.close()
     ctx.close()
+
+
+def f64_compare(args, dist, B, stream):
+    """The spec ratio: one solve with the plain FP64 filter against one
+    with the FP32 defect-corrected filter (after a warm-up solve that tunes its
+    kernel) on `--f64-compare`'s workload, both to ||r|| <= 1e-10 ||A||.
+    Reports both rates, the speed-up, and per result the eigenvalue difference
+    between the two forms and each form's relative residual (for Hermitian A a
+    residual bounds the distance of the Ritz value to the spectrum)."""
+    import numpy as np
+    import torch
+    from synth import workloads
+    w = workloads.WORKLOADS[args.f64_compare]()
+    A = w.matrix()
+    ctx = B.Context(dist.local, stream=stream.cuda_stream)
+    M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(prec):
+        prm = B.default_params(a=w.a, b=w.b, p=w.p, seed=w.seed, filter_precision=prec, max_iter=args.max_iter)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        r = B.solve(ctx, M, prm, allow_no_convergence=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        out = dict(ms=ev0.elapsed_time(ev1), status=r.status, lam=r.eigvals(), res=r.residuals(),
+                   st=r.stats())
+        r.close()
+        return out
+
+    timed(B.APF_FILTER_F32_DEFECT)  # warm-up: kernel tuning of this matrix
+    f32 = timed(B.APF_FILTER_F32_DEFECT)
+    f64 = timed(B.APF_FILTER_F64)
+    M.close()
+    ctx.close()
+
+    def arm(o):
+        e = int(o["lam"].size)
+        return {"value": e / (o["ms"] / 1e3), "unit": UNIT, "seconds": o["ms"] / 1e3, "eigenpairs": e,
+                "status": o["status"], "iterations": o["st"]["iterations"],
+                "max_residual": float(o["res"].max()) if e else None}
+
+    same = f32["lam"].size == f64["lam"].size
+    norm_a = f64["st"]["norm_a"]
+    dl = (np.abs(f32["lam"] - f64["lam"]) / norm_a) if same else None
+    a32, a64 = arm(f32), arm(f64)
+    return {"workload": args.f64_compare, "n": A.n, "p": w.p, "interval": [w.a, w.b],
+            "f32_defect": a32, "f64": a64,
+            "speedup_vs_plain_f64": a32["value"] / a64["value"] if a64["value"] else None,
+            "same_count": bool(same),
+            "max_dlambda_over_normA": float(dl.max()) if dl is not None and dl.size else None,
+            "per_result": {"dlambda_over_normA": [float(f"{x:.3g}") for x in dl] if dl is not None else None,
+                           "residual_f32_defect": [float(f"{x:.3g}") for x in f32["res"]],
+                           "residual_f64": [float(f"{x:.3g}") for x in f64["res"]]}}
 
 
 def serving_arm(args, dist):

@@ -89,7 +89,7 @@ typedef struct {
   double k_ratio;           /* maximum degree k = ceil(k_ratio * k^(1)), 2.5 */
   double m_d;               /* damping exponent m of Eq. (m_Lanczos_damping), 0.5 */
   double tau_a;             /* adaptive threshold of Alg. 3, 1e-3 */
-  double tau_c;             /* convergence threshold: lock when ||r|| <= tau_c ||A||, 1e-10 */
+  double tau_c;             /* convergence threshold: lock when ||r|| <= tau_c ||A||, 1e-10 (||A||: apf_stats.norm_a) */
   int32_t max_iter;         /* outer iteration cap, 50 */
   int32_t lanczos_steps;    /* Lanczos steps for the spectrum bounds (Sec. 3.4), 40 */
   double bound_pad;         /* outward padding of the bounds, fraction of the Ritz spread, 0.01 */
@@ -114,7 +114,7 @@ typedef struct {
   int64_t filter_launches;   /* Clenshaw step kernels launched */
   int64_t gpu_launches;      /* all kernels launched by this solve */
   double lambda_min, lambda_max;  /* estimated spectrum bounds */
-  double norm_a;             /* max(|lambda_min|, |lambda_max|) */
+  double norm_a;             /* ||A|| of the convergence test: max |theta| over the Lanczos Ritz values (<= the spectral radius) */
   double ms_total, ms_setup, ms_filter, ms_orth, ms_rr, ms_check;  /* stage wall times */
   double filter_kernel_ms;   /* summed device time of the Clenshaw SpMM launches (CUDA events) */
   double filter_bytes;       /* algorithmic bytes of those launches */
@@ -139,6 +139,26 @@ const char* apf_status_string(int status);
 const char* apf_last_error_message(const apf_ctx* ctx);
 /* Kernels launched on this context since creation (a counter). */
 int64_t apf_launch_count(const apf_ctx* ctx);
+
+/* Time limit of every device-side wait of this context's kernels: the filter
+ * kernels' shared-memory barrier and two-step dependency waits, and the small
+ * eigensolver's grid barrier.  A wait that runs out makes the kernel record a
+ * timeout, let its own copies land and return; the call then fails with
+ * APF_ERR_TIMEOUT and the context stays usable.  ns = 0 restores the defaults
+ * (1 s for the filter waits, 2 s for the grid barrier); at most 60 s, else
+ * APF_ERR_ARG.  The paper has no counterpart: its CPU code has no device
+ * waits. */
+apf_status apf_set_wait_limit(apf_ctx* ctx, int64_t ns);
+/* Failure-path check, with no counterpart in the paper: launch a kernel whose
+ * device-side wait nothing will satisfy and return the status the library
+ * makes of it (APF_ERR_TIMEOUT when the wait gave up as it should).
+ * which = 0: the two-step filter pass (Alg. 2, two Clenshaw steps per pass)
+ * over A's SELL copy, with every second step waiting for dependency counts
+ * that are never reached (A needs a SELL copy and n > 32, else APF_ERR_ARG);
+ * which = 1: the eigensolver's grid barrier, waiting for one block more than
+ * the launch has (A unused, may be NULL).  Each waiting block gives up after
+ * the limit of apf_set_wait_limit: set a short one first. */
+apf_status apf_wait_probe(apf_ctx* ctx, const apf_matrix* A, int32_t which);
 
 /* ---- matrices ---------------------------------------------------------- */
 
@@ -214,7 +234,9 @@ apf_status apf_result_eigvals(const apf_result* r, double* host_out);
  * belongs to eigenvalue j), of the matrix dtype; `out_on_device` selects
  * where `out` lives. */
 apf_status apf_result_eigvecs(const apf_result* r, void* out, int64_t ld, int32_t out_on_device);
-/* e relative residuals ||A v - lambda v|| / ||A|| to host memory. */
+/* e relative residuals ||A v - lambda v|| / norm_a to host memory (norm_a
+ * never exceeds the spectral radius, so these bound the residuals relative to
+ * the true ||A|| from above). */
 apf_status apf_result_residuals(const apf_result* r, double* host_out);
 apf_status apf_result_stats(const apf_result* r, apf_stats* out);
 /* Per-iteration history, up to `cap` records of 6 doubles each:
@@ -263,7 +285,8 @@ apf_status apf_server_submit(apf_server* s, int64_t n, int64_t nnz, const int64_
 /* Block until the request is done; return its status.  *out receives its
  * result (as apf_solve gives it; NULL when the solve failed), which owns the
  * request's context: apf_result_destroy releases both.  `info` (nullable)
- * receives the request's times.  A ticket can be waited for once. */
+ * receives the request's times.  A ticket can be waited for once: a second
+ * wait, also from another thread while the first blocks, gives APF_ERR_ARG. */
 apf_status apf_server_wait(apf_server* s, int64_t ticket, apf_result** out, apf_request_info* info);
 apf_status apf_server_state(apf_server* s, apf_server_info* out);
 /* Finish every queued request, stop the workers, free the results nobody
@@ -362,8 +385,9 @@ apf_status apf_rayleigh_ritz(apf_ctx* ctx, const apf_matrix* A, const void* Q, i
 apf_status apf_residual_norms(apf_ctx* ctx, const apf_matrix* A, const void* V, int64_t ld,
                               int64_t p, const double* w, double* host_out);
 
-/* G = X^H Y exactly as apf_gram computes it, for callers that cannot allocate
- * device memory (code inside a CUDA graph being captured, an allocator's own
+/* G = X^H Y as apf_gram computes it, to the same FP64 tolerance (not bit for
+ * bit: the array below caps the number of row splits, so the summation order
+ * can differ), for callers that cannot allocate device memory (code inside a CUDA graph being captured, an allocator's own
  * callbacks, a host with a fixed memory budget).  The paper has no
  * counterpart: this is a deployment variant of the Gram step.
  * It takes no context and allocates nothing: the partial sums of its row
@@ -374,7 +398,9 @@ apf_status apf_residual_norms(apf_ctx* ctx, const apf_matrix* A, const void* V, 
  * ordered on `cuda_stream` (a cudaStream_t, NULL for the legacy default
  * stream).  The first call on each device looks up the array's device address
  * with cudaGetSymbolAddress while that device is current: make that first
- * call before any stream capture.  All calls on a device share the array and
+ * call before any stream capture.  A device reset (cudaDeviceReset) makes a
+ * new context: the first call after it looks the address up again, so it too
+ * belongs before any capture.  All calls on a device share the array and
  * it keeps the last call's contents (no call needs it cleared); calls whose
  * work overlaps on the GPU (different streams, no ordering) race on it. */
 apf_status apf_gram_noalloc(int32_t dtype, int64_t n, int64_t pa, int64_t pb, const void* X,

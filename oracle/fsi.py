@@ -18,8 +18,11 @@ Readings taken where the paper is silent or ambiguous:
 * When the first Cholesky factorisation of CholQR2 meets a non-positive pivot,
   the shifted Cholesky QR of Fukaya et al. (SIAM J. Sci. Comput. 2020) with
   shift 11 (n p + p (p + 1)) u ||X||_F^2 runs first (CholQR3).
-* Locking uses ||r_j|| <= tau_c ||A|| with ||A|| = max(|lmin|, |lmax|),
-  the convergence test of Sec. 4.
+* Locking uses ||r_j|| <= tau_c ||A||, the convergence test of Sec. 4, with
+  ||A|| = max(|theta_min|, |theta_max|) from the Lanczos Ritz values: they lie
+  inside the spectrum, so this never exceeds the true spectral radius and a
+  locked pair satisfies ||r_j|| <= tau_c ||A|| for the true ||A|| (the padded
+  bounds lmin, lmax, which contain the spectrum, serve the map l only).
 * n_check^(i-1) is the value from the last iteration that computed it (0 at
   the start); iterations with e^(i) = 0 leave it and the degree unchanged.
 * The loop stops after ``max_iter`` iterations with status "no_convergence"
@@ -187,7 +190,7 @@ def setup(A, a: float, b: float, params: Params, v0_lanczos: np.ndarray):
     """Set-up of Alg. 4: l1, l2, ||A||, degrees and the coefficients a_j."""
     lmin, lmax, binfo = lanczos_bounds(A, params.lanczos_steps, v0_lanczos, params.bound_pad)
     l1, l2 = cb.linear_map(lmin, lmax)
-    normA = max(abs(lmin), abs(lmax))
+    normA = max(abs(binfo["theta_min"]), abs(binfo["theta_max"]))
     am, bm = l1 * a + l2, l1 * b + l2
     if not (-1.0 < am < bm < 1.0):
         raise ValueError("interval [a, b] must lie inside the estimated spectrum")

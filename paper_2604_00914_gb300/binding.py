@@ -118,6 +118,8 @@ SIGNATURES = {
     "apf_status_string": (C.c_char_p, [C.c_int]),
     "apf_last_error_message": (C.c_char_p, [_P]),
     "apf_launch_count": (_I64, [_P]),
+    "apf_set_wait_limit": (_I32, [_P, _I64]),
+    "apf_wait_probe": (_I32, [_P, _P, _I32]),
     "apf_matrix_create_csr": (_I32, [_P, _I64, _I64, _P, _P, _P, _I32, _I32, C.POINTER(_P)]),
     "apf_matrix_create_sell": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _I32, C.POINTER(_P)]),
     "apf_matrix_destroy": (_I32, [_P]),
@@ -239,6 +241,14 @@ class Context:
 
     def launch_count(self):
         return int(self.lib.apf_launch_count(self.h))
+
+    def set_wait_limit(self, ns):
+        """apf_set_wait_limit: time limit of the device-side waits (0: defaults)."""
+        self.lib.check(self.lib.apf_set_wait_limit(self.h, int(ns)), self.h)
+
+    def wait_probe(self, which, matrix=None):
+        """apf_wait_probe: the status of a kernel whose wait nothing satisfies."""
+        return int(self.lib.apf_wait_probe(self.h, matrix.h if matrix is not None else None, int(which)))
 
 
 class Matrix:

@@ -50,8 +50,16 @@ struct apf_ctx {
   int64_t launches = 0;          // kernels launched through this context
   double* h_pinned = nullptr;    // pinned staging buffer
   size_t h_pinned_bytes = 0;
+  uint64_t wait_limit_ns = 0;    // device-side wait limit (apf_set_wait_limit); 0: the defaults below
   std::string last_error;
 };
+
+// Time limits of the device-side waits: the filter kernels' mbarrier and
+// two-step dependency waits (1 s), the eigensolver's grid barrier (2 s).
+constexpr uint64_t kFilterWaitNs = 1000000000ull;
+constexpr uint64_t kBarrierWaitNs = 2000000000ull;
+inline uint64_t filter_wait_ns(const apf_ctx* c) { return c->wait_limit_ns ? c->wait_limit_ns : kFilterWaitNs; }
+inline uint64_t barrier_wait_ns(const apf_ctx* c) { return c->wait_limit_ns ? c->wait_limit_ns : kBarrierWaitNs; }
 
 struct apf_matrix {
   apf_ctx* ctx = nullptr;

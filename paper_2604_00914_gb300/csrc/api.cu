@@ -91,6 +91,21 @@ apf_status apf_destroy(apf_ctx* ctx) {
 
 int64_t apf_launch_count(const apf_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+apf_status apf_set_wait_limit(apf_ctx* ctx, int64_t ns) {
+  if (!ctx || ns < 0 || ns > 60000000000LL) return APF_ERR_ARG;
+  ctx->wait_limit_ns = (uint64_t)ns;
+  return APF_OK;
+}
+
+apf_status apf_wait_probe(apf_ctx* ctx, const apf_matrix* A, int32_t which) {
+  if (!ctx || (which != 0 && which != 1) || (which == 0 && (!A || A->ctx != ctx))) return APF_ERR_ARG;
+  APF_TRY(ctx)
+  bind(ctx);
+  if (which == 0) apf::wait_probe_pair(ctx, A);
+  else apf::wait_probe_barrier(ctx);
+  APF_CATCH(ctx)
+}
+
 void apf_params_default(apf_params* p) {
   if (!p) return;
   memset(p, 0, sizeof(*p));

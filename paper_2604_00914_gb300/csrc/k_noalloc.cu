@@ -11,7 +11,13 @@
 // kNoAllocScratchBytes of device memory until the process exits.  Host code
 // cannot use the array's name as a device address (it denotes a host-side
 // stand-in), so the first call on each device looks up the device address
-// with cudaGetSymbolAddress while that device is current and caches it.
+// with cudaGetSymbolAddress while that device is current and caches it.  The
+// cache remembers the context the address belongs to: after a device reset
+// (cudaDeviceReset) the runtime creates a new context and loads the module
+// again, and the next call looks the address up again instead of using the
+// stale one.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "apf_internal.h"
@@ -26,26 +32,56 @@ static __device__ __align__(256) unsigned char g_gram_scratch[kNoAllocScratchByt
 struct DeviceScratch {
   void* ptr = nullptr;
   int num_sms = 0;
+  unsigned long long ctx_id = 0;  // context the address belongs to
   bool ready = false;
 };
 std::mutex g_scratch_mutex;
 DeviceScratch g_scratch[kMaxDevices];
 
-// Set-up for the current device (first call only): the device address of the
-// array and the SM count.
+// The unique id of the calling thread's current context, 0 when there is none
+// (driver entry points through the runtime: nothing links libcuda directly).
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || c == nullptr) return 0;
+  if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Set-up for the current device (first call, and the first call in a new
+// context of it): the device address of the array and the SM count.
 apf_status scratch_for_current_device(DeviceScratch* out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return APF_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return APF_ERR_ARG;
+  const unsigned long long id = current_context_id();
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
   DeviceScratch& d = g_scratch[dev];
-  if (!d.ready) {
+  if (!d.ready || id == 0 || id != d.ctx_id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_gram_scratch) != cudaSuccess) return APF_ERR_CUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return APF_ERR_CUDA;
     d.ptr = p;
     d.num_sms = sms;
+    d.ctx_id = current_context_id();  // the context now exists
     d.ready = true;
   }
   *out = d;

@@ -182,7 +182,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 // Grid barrier for a cooperative launch.  bar[0]: arrivals, bar[1]: generation.
 // Returns false (and records DEV_BARRIER_TIMEOUT) if the other blocks do not
 // arrive within the time limit; callers then leave the kernel.
-__device__ bool grid_barrier(unsigned* bar, unsigned& gen, unsigned nblocks, int* err) {
+__device__ bool grid_barrier(unsigned* bar, unsigned& gen, unsigned nblocks, int* err, uint64_t limit_ns) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -197,7 +197,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned& gen, unsigned nblocks, int
       const uint64_t t0 = global_ns();
       while (atomicAdd(&bar[1], 0u) == gen) {
         __nanosleep(64);
-        if (global_ns() - t0 > 2000000000ull) {  // 2 s
+        if (global_ns() - t0 > limit_ns) {  // 2 s unless the context sets another limit
           set_err(err, DEV_BARRIER_TIMEOUT);
           ok = 0;
           break;
@@ -219,7 +219,7 @@ __device__ __forceinline__ int rr_index(int pos, int r, int P) {
 template <class T>
 __global__ void __launch_bounds__(128) k_jacobi_sweeps(int p, int P, T* M, unsigned* bar,
                                                        unsigned* counters, int max_sweeps,
-                                                       double tol, int* err) {
+                                                       double tol, int* err, uint64_t limit_ns) {
   const int lane = threadIdx.x % 32;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int nw = gridDim.x * blockDim.x / 32;
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(128) k_jacobi_sweeps(int p, int P, T* M, unsig
           if (lane == 0) atomicAdd(&counters[sweep], 1u);
         }
       }
-      if (!grid_barrier(bar, gen, gridDim.x, err)) return;
+      if (!grid_barrier(bar, gen, gridDim.x, err, limit_ns)) return;
     }
     if (atomicAdd(&counters[sweep], 0u) == 0u) return;  // a sweep without rotations
   }
@@ -356,13 +356,36 @@ void eigh_jacobi(apf_ctx* ctx, int64_t p, const T* B, int64_t ldb, double* w, T*
   int* err = ctx->d_err;
   int ms = max_sweeps;
   int Pv = P;
-  void* args[] = {&pi, &Pv, &M, &bar, &counters, &ms, &tol, &err};
+  uint64_t limit = barrier_wait_ns(ctx);
+  void* args[] = {&pi, &Pv, &M, &bar, &counters, &ms, &tol, &err, &limit};
   APF_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_sweeps<T>, dim3(nb), dim3(threads), args, 0,
                                        ctx->stream));
   k_jacobi_finish<T><<<(unsigned)p, 128, 0, ctx->stream>>>((int)p, M, B, ldb, lam);
   k_jacobi_sort<T><<<1, 1024, 0, ctx->stream>>>((int)p, lam, M, w, U, ldu);
   count_launch(ctx, 3);
 }
+// Failure-path check of the eigensolver's grid barrier: the blocks of a
+// cooperative launch wait for one more arrival than there are blocks, which
+// never comes; each gives up after the context's wait limit.
+__global__ void k_barrier_probe(unsigned* bar, int* err, uint64_t limit_ns) {
+  unsigned gen = 0;
+  grid_barrier(bar, gen, gridDim.x + 1, err, limit_ns);
+}
+
+void wait_probe_barrier(apf_ctx* ctx) {
+  APF_CUDA(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
+  unsigned* bar = ctx->d_bar;
+  int* err = ctx->d_err;
+  uint64_t limit = barrier_wait_ns(ctx);
+  void* args[] = {&bar, &err, &limit};
+  APF_CUDA(cudaLaunchCooperativeKernel((void*)k_barrier_probe, dim3(2), dim3(128), args, 0, ctx->stream));
+  count_launch(ctx);
+  APF_CUDA(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
+  const int e = fetch_device_error(ctx);
+  if (e == DEV_BARRIER_TIMEOUT) throw ApfError{APF_ERR_TIMEOUT, "eigensolver grid barrier"};
+  if (e != 0) throw ApfError{APF_ERR_CUDA, "device error in the wait probe"};
+}
+
 template void eigh_jacobi<double>(apf_ctx*, int64_t, const double*, int64_t, double*, double*, int64_t);
 template void eigh_jacobi<double2>(apf_ctx*, int64_t, const double2*, int64_t, double*, double2*,
                                    int64_t);

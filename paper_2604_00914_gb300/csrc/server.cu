@@ -40,6 +40,7 @@ struct Request {
   apf_status status = APF_OK;
   apf_result* result = nullptr;
   bool done = false;
+  bool claimed = false;  // a thread waits for it (a ticket can be waited for once)
 };
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
@@ -229,7 +230,11 @@ apf_status apf_server_wait(apf_server* s, int64_t ticket, apf_result** out, apf_
     auto it = s->reqs.find(ticket);
     if (it == s->reqs.end()) return APF_ERR_ARG;
     Request* rp = it->second.get();
+    if (rp->claimed) return APF_ERR_ARG;  // another thread already waits for it
+    rp->claimed = true;
     s->cv_done.wait(lk, [&] { return rp->done; });
+    // the entry stays in the map while claimed: look it up again after the wait
+    it = s->reqs.find(ticket);
     r = std::move(it->second);
     s->reqs.erase(it);
   }

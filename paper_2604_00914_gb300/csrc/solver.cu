@@ -1223,7 +1223,10 @@ static Bounds setup_bounds(apf_ctx* ctx, const apf_matrix* A, const apf_params* 
   B.lmax = bnd[1];
   B.l1 = 2.0 / (B.lmax - B.lmin);
   B.l2 = -(B.lmax + B.lmin) / (B.lmax - B.lmin);
-  B.normA = std::max(fabs(B.lmin), fabs(B.lmax));
+  // ||A|| of the convergence test (Sec. 4) from the unpadded Lanczos Ritz
+  // values: they lie inside the spectrum, so this never exceeds the spectral
+  // radius and ||r|| <= tau_c ||A|| holds for the true ||A|| at locking
+  B.normA = std::max(fabs(bnd[2]), fabs(bnd[3]));
   return B;
 }
 
@@ -1597,6 +1600,31 @@ void residual_norms_public(apf_ctx* ctx, const apf_matrix* A, const T* V, int64_
   residual_norms<T>(ctx, n, p, AV.as<T>(), Vb.as<T>(), ld, w, rd.as<double>(), nullptr, 0.0);
   APF_CUDA(cudaMemcpyAsync(host_out, rd.p, (size_t)p * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   APF_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+// Failure-path check of the two-step filter pass: one pass over the matrix's
+// SELL copy (FP32, width 8, zero values) in which every step-2 item waits for
+// step-1 counts of pass 1000, which the counters (zero before the launch, so
+// at most 1 after it) never reach.  Every waiting CTA gives up after the
+// context's wait limit, records DEV_BARRIER_TIMEOUT and leaves; the host turns
+// that into APF_ERR_TIMEOUT.
+void wait_probe_pair(apf_ctx* ctx, const apf_matrix* A) {
+  APF_REQUIRE(A->sell_ok, APF_ERR_ARG);
+  const int G = 32, VPT = 1;
+  const int R = 256 / G;
+  APF_REQUIRE((int64_t)R * 4 < A->n, APF_ERR_ARG);
+  const int64_t n = A->n, ld = 8;
+  DBuf vals((size_t)A->sell_slots * sizeof(float), ctx->stream, true);
+  DBuf a((size_t)n * ld * sizeof(float), ctx->stream, true), b((size_t)n * ld * sizeof(float), ctx->stream, true);
+  DBuf y((size_t)n * ld * sizeof(float), ctx->stream, true);
+  const size_t segs = (size_t)((n + 8 * PAIR_SEG - 1) / (8 * PAIR_SEG) + 1) * sizeof(unsigned);
+  DBuf seg(segs, ctx->stream, true);
+  clenshaw_sell_pair<float, float>(ctx, G, VPT, n, A->sell_chunk_ptr, A->sell_col, vals.as<float>(), A->sell_lmax,
+                                   A->sell_bw, a.as<float>(), b.as<float>(), nullptr, y.as<float>(), ld, ld,
+                                   nullptr, 0.5f, nullptr, 0.25f, seg.as<unsigned>(), 1000u);
+  const int e = fetch_device_error(ctx);
+  if (e == DEV_BARRIER_TIMEOUT) throw ApfError{APF_ERR_TIMEOUT, "two-step filter dependency wait"};
+  if (e != 0) throw ApfError{APF_ERR_CUDA, "device error in the wait probe"};
 }
 
 #define APF_INST(T)                                                                                  \

@@ -43,6 +43,10 @@ void cholqr2_public(apf_ctx* ctx, int64_t n, int64_t p, T* X, int64_t ld);
 template <class T>
 void rayleigh_ritz_public(apf_ctx* ctx, const apf_matrix* A, const T* Q, int64_t ld, int64_t p,
                           double* w, T* V, int64_t ldv);
+// failure-path checks: kernels whose device-side wait nothing satisfies
+void wait_probe_pair(apf_ctx* ctx, const apf_matrix* A);
+void wait_probe_barrier(apf_ctx* ctx);
+
 template <class T>
 void residual_norms_public(apf_ctx* ctx, const apf_matrix* A, const T* V, int64_t ld, int64_t p,
                            const double* w, double* host_out);

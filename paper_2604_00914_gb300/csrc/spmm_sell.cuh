@@ -15,7 +15,8 @@
 // dependent chain per row is thus: one round for the structure (overlapped
 // with the Y / Vin staging), the gathers, the store.
 //
-// Every wait on the mbarrier is bounded in time; on expiry the kernel records
+// Every wait on the mbarrier is bounded in time (limit_ns, a kernel argument:
+// 1 s unless the context sets another); on expiry the kernel records
 // DEV_BARRIER_TIMEOUT, waits (bounded) for its copies and returns.
 #pragma once
 #include <atomic>
@@ -102,7 +103,7 @@ __device__ __forceinline__ bool sell_tile(
     const TA* __restrict__ sval, int lmax, const T* W, const T* Vin, const T* Y, int64_t ld, int nvec,
     const typename ScalarTraits<T>::Real* __restrict__ coef_col, typename ScalarTraits<T>::Real coef_scalar,
     typename ScalarTraits<T>::Real alpha, T* Out, unsigned char* smem, uint64_t* bar, uint32_t parity,
-    int* err, const Wait& wait) {
+    int* err, uint64_t limit_ns, const Wait& wait) {
   using Real = typename ScalarTraits<T>::Real;
   constexpr int E = ScalarTraits<T>::per16;
   constexpr int R = 256 / G;
@@ -134,10 +135,12 @@ __device__ __forceinline__ bool sell_tile(
     mbar_arrive(bar);
   }
   const bool ready = wait();
-  const bool landed = mbar_wait_bounded(bar, parity, 1000000000ull);
+  const bool landed = mbar_wait_bounded(bar, parity, limit_ns);
   if (!__syncthreads_and(ready && landed)) {  // one decision for the whole CTA
     if (threadIdx.x == 0) atomicCAS(err, 0, DEV_BARRIER_TIMEOUT);
-    mbar_wait_bounded(bar, parity, 1000000000ull);  // let the copies land before leaving
+    // let the copies land before leaving (they complete by themselves; the
+    // limit is at least the default so a short test limit cannot cut it off)
+    mbar_wait_bounded(bar, parity, limit_ns > 1000000000ull ? limit_ns : 1000000000ull);
     return false;
   }
 
@@ -207,7 +210,7 @@ k_clenshaw_sell(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32_t*
                 const T* __restrict__ Y, int64_t ld, int nvec,
                 const typename ScalarTraits<T>::Real* __restrict__ coef_col,
                 typename ScalarTraits<T>::Real coef_scalar, typename ScalarTraits<T>::Real alpha, T* Out,
-                int* err) {
+                int* err, uint64_t limit_ns) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   if (threadIdx.x == 0) {
@@ -217,7 +220,8 @@ k_clenshaw_sell(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32_t*
   __syncthreads();
   constexpr int R = 256 / G;
   sell_tile<T, TA, G, VPT, false>((int64_t)blockIdx.x * R, n, chunk_ptr, scol, sval, lmax, W, Vin, Y, ld,
-                                  nvec, coef_col, coef_scalar, alpha, Out, smem, bar, 0u, err, NoWait());
+                                  nvec, coef_col, coef_scalar, alpha, Out, smem, bar, 0u, err, limit_ns,
+                                  NoWait());
 }
 
 // ---- two Clenshaw steps in one pass (temporal blocking) -----------------------------
@@ -242,6 +246,7 @@ struct PairDeps {
   const unsigned* seg_count;
   int t, halo, ntiles;
   unsigned pass;
+  uint64_t limit_ns;
   __device__ bool operator()() const {
     const int lo = (t - halo > 0 ? t - halo : 0) / PAIR_SEG;
     const int hi = (t + halo < ntiles - 1 ? t + halo : ntiles - 1) / PAIR_SEG;
@@ -255,7 +260,7 @@ struct PairDeps {
         if (have < pass * (unsigned)cnt) mine = false;
       }
       if (__syncthreads_and(mine)) break;
-      if (__syncthreads_or(sell_ns() - t0 > 1000000000ull)) return false;
+      if (__syncthreads_or(sell_ns() - t0 > limit_ns)) return false;
       __nanosleep(128);
     }
     __threadfence();
@@ -283,6 +288,7 @@ struct PairArgs {
   unsigned* seg_count;
   unsigned pass;
   int* err;
+  uint64_t limit_ns;
 };
 
 __device__ __forceinline__ void pair_item(int q, int ntiles, int lag, int* kind, int* t) {
@@ -326,11 +332,13 @@ k_clenshaw_sell_pair(PairArgs a) {
     bool ok;
     if (kind == 1) {
       ok = sell_tile<T, TA, G, VPT, false>(r0, a.n, a.chunk_ptr, a.scol, sval, a.lmax, A, Va, Y, a.ld, a.nvec,
-                                           f1, (Real)a.coef1, (Real)2, Bb, smem, bar, parity, a.err, NoWait());
+                                           f1, (Real)a.coef1, (Real)2, Bb, smem, bar, parity, a.err, a.limit_ns,
+                                           NoWait());
     } else {
-      PairDeps deps{a.seg_count, t, a.halo, a.ntiles, a.pass};
+      PairDeps deps{a.seg_count, t, a.halo, a.ntiles, a.pass, a.limit_ns};
       ok = sell_tile<T, TA, G, VPT, true>(r0, a.n, a.chunk_ptr, a.scol, sval, a.lmax, Bb, A, Y, a.ld, a.nvec,
-                                          f2, (Real)a.coef2, (Real)2, A, smem, bar, parity, a.err, deps);
+                                          f2, (Real)a.coef2, (Real)2, A, smem, bar, parity, a.err, a.limit_ns,
+                                          deps);
     }
     parity ^= 1u;
     if (!ok) return;
@@ -383,7 +391,8 @@ void clenshaw_sell_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t
     auto kern = k_clenshaw_sell<T, TA, GG, VV>;                                                      \
     allow_large_smem<k_clenshaw_sell<T, TA, GG, VV>>(ctx->device);                                   \
     kern<<<grid, 256, smem, ctx->stream>>>(n, chunk_ptr, scol, sval, lmax, W, Vin, Y, ld, nvec,      \
-                                           coef_col, coef_scalar, alpha, Out, ctx->d_err);           \
+                                           coef_col, coef_scalar, alpha, Out, ctx->d_err,            \
+                                           filter_wait_ns(ctx));                                     \
     launched = true;                                                                                 \
   }
   APF_SELL_CASE(8, 1) APF_SELL_CASE(8, 2) APF_SELL_CASE(8, 3) APF_SELL_CASE(8, 4)
@@ -435,6 +444,7 @@ void clenshaw_sell_pair_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const in
   a.seg_count = seg_count;
   a.pass = pass;
   a.err = ctx->d_err;
+  a.limit_ns = filter_wait_ns(ctx);
   bool launched = false;
 #define APF_PAIR_CASE(GG, VV)                                                                         \
   if (G == GG && VPT == VV) {                                                                         \

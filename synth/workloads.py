@@ -99,6 +99,21 @@ def anderson3d_c_48() -> Workload:
 
 _BUILDERS["anderson3d_c_48"] = lambda seed: matrices.anderson(48, 3, 4.0, seed, complex_phases=True)
 
+
+def anderson3d_c_40() -> Workload:
+    """The 64^3 workload's model on a 40^3 grid (n = 64,000), p = 160, with the
+    interval widened by the ratio of the sizes (262,144 / 64,000) so that it
+    holds about the same number of eigenvalues (about 100) at the same density
+    of states: the case on which the plain FP64 path and the FP32 forms are
+    timed against each other (its FP32 blocks, 82 MB, and the three of them
+    that one step touches still exceed what L2 keeps)."""
+    h = ANDERSON64_HALFWIDTH * 262144.0 / 64000.0
+    return Workload("anderson3d_c_40", BASE_SEED + 13, 160, -h, h, True,
+                    "3D Anderson 40^3 periodic, Peierls phases, W=4, complex, p=160")
+
+
+_BUILDERS["anderson3d_c_40"] = lambda seed: matrices.anderson(40, 3, 4.0, seed, complex_phases=True)
+
 @dataclass
 class SliceWorkload:
     """Several disjoint intervals of one matrix (spectrum slicing)."""
@@ -136,6 +151,7 @@ WORKLOADS = {
     "lap2d_32": lap2d_32,
     "anderson3d_c_64": anderson3d_c_64,
     "anderson3d_c_48": anderson3d_c_48,
+    "anderson3d_c_40": anderson3d_c_40,
 }
 
 SLICE_WORKLOADS = {

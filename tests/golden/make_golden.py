@@ -13,6 +13,14 @@ Run from the repository root:  python tests/golden/make_golden.py
   estimate (oracle.trace: Hutchinson trace of a degree-4000 step filter over
   16 +-1 probes, bounds from the Gershgorin interval), cut into eight slices
   of equal width; and the estimated count of each slice.
+* interval_ks8_96.json -- the interval of the 96^3 Kohn-Sham-like workload:
+  [E_300, E_500], where E_N is the energy below which the oracle's count
+  estimate finds N eigenvalues (oracle.trace: Chebyshev moments of degree
+  3000 over 16 +-1 probes, i.e. the Hutchinson trace of the degree-3000 step
+  filter of [lambda_min, E], bounds from the Gershgorin interval), so that the
+  interval holds about 200 eigenvalues around the midpoint of the 300th-500th.
+
+    python tests/golden/make_golden.py [lap2d | slices48 | ks96]   (default: all)
 """
 from __future__ import annotations
 
@@ -83,6 +91,45 @@ def slices_anderson48(target=240, nslices=8, k=4000, probes=16):
     print("anderson3d_r_48 slices: w", w, "counts", [round(c, 1) for c in counts])
 
 
+def ks8_96_interval(lo_count=300, hi_count=500, k=3000, probes=16):
+    seed = BASE_SEED + 2
+    A = matrices.ks_like_3d(96, seed, n_wells=64, sigma=1.5).to_scipy()
+    lmin, lmax = fsi.gershgorin(A)
+    l1, l2 = cb.linear_map(lmin, lmax)
+    Z = rng.rademacher_block(seed, rng.STREAM_TEST, A.shape[0], probes)
+    mu = trace.chebyshev_trace_moments(A, l1, l2, Z, k)
+
+    def below(E):  # estimated number of eigenvalues in [lmin, E]
+        coef = cb.filter_coefficients(-1.0, l1 * E + l2, k, cb.DAMP_LANCZOS_M, 0.5)
+        return float(coef @ mu)
+
+    def energy_at(count):  # bisection on the monotone estimate
+        lo, hi = lmin, lmax
+        for _ in range(100):
+            mid = 0.5 * (lo + hi)
+            if below(mid) < count:
+                lo = mid
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+
+    a, b = energy_at(lo_count), energy_at(hi_count)
+    out = dict(a=a, b=b, count_estimate=below(b) - below(a), lo_count=lo_count, hi_count=hi_count,
+               gershgorin=[lmin, lmax], degree=k, probes=probes,
+               count_below_zero=below(0.0),
+               source=("oracle.trace.chebyshev_trace_moments (degree %d, %d probes of stream %d) on "
+                       "synth.matrices.ks_like_3d(96, %d, n_wells=64, sigma=1.5); Gershgorin bounds" %
+                       (k, probes, rng.STREAM_TEST, seed)))
+    with open(os.path.join(HERE, "interval_ks8_96.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print("ks8_96:", a, b, "estimated count", out["count_estimate"])
+
+
 if __name__ == "__main__":
-    lap2d_interval()
-    slices_anderson48()
+    which = sys.argv[1:] or ["lap2d", "slices48", "ks96"]
+    if "lap2d" in which:
+        lap2d_interval()
+    if "slices48" in which:
+        slices_anderson48()
+    if "ks96" in which:
+        ks8_96_interval()

@@ -20,9 +20,12 @@ def empty_like_np(shape, is_complex):
 
 
 def clenshaw_tol(coef, X, eps):
-    """Error bound used for Alg. 2 parity: the recurrence runs k steps, each
-    adding a rounding error of order eps times the largest intermediate, and
-    the Clenshaw intermediates are bounded by sum |a_j| times ||X||_max; a
-    factor 50 covers the row length of the sparse products."""
+    """Error bound used for Alg. 2 parity.  The recurrence runs k steps; each
+    adds a rounding error of order eps times the Clenshaw intermediates, which
+    the filter keeps near sum |a_j| max|X|, and errors of independent sign add
+    like a random walk: sqrt(k) eps sum|a_j| max|X|, with a margin of 4.
+    tests/test_tolerances.py checks that an FP32 evaluation in another
+    summation order stays well inside this bound, and that dropping any one
+    a_j T_j term, the smallest plausible slip in the recurrence, exceeds it."""
     k = len(coef) - 1
-    return 50.0 * max(k, 1) * eps * max(1.0, float(np.sum(np.abs(coef)))) * float(np.max(np.abs(X)))
+    return 4.0 * np.sqrt(max(k, 1)) * eps * max(1.0, float(np.sum(np.abs(coef)))) * float(np.max(np.abs(X)))

@@ -75,7 +75,8 @@ def _check_against_definition(out, A, lam, a, b, tol=1e-10):
     V = out["V"]
     R = A.to_scipy() @ V - V * out["lam"]
     res = np.linalg.norm(R, axis=0)
-    assert res.max() <= tol * norm_est * (1 + 1e-6)
+    assert norm_est <= normA * (1 + 1e-12)
+    assert res.max() <= tol * normA
     assert np.max(np.abs(out["res"] - res / norm_est)) < 1e-12
     # within a slice the vectors come out of one Rayleigh-Ritz basis; across
     # slices |v_i^H v_j| <= (||r_i|| + ||r_j||) / |lam_i - lam_j| (Davis-Kahan)

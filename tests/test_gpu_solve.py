@@ -48,16 +48,18 @@ def _solve(B, ctx, A, a, b, p, seed, **kw):
 
 def _check(out, A, lam_ref, tol=1e-10):
     As = A.to_scipy()
-    normA = np.abs(np.linalg.eigvalsh(A.to_dense())).max() if A.n <= 4096 else out["stats"]["norm_a"]
+    # ||A|| is the true spectral radius (dense eigh)
+    normA = np.abs(np.linalg.eigvalsh(A.to_dense())).max()
     assert out["status"] == 0
     assert out["lam"].size == lam_ref.size, (out["lam"].size, lam_ref.size)
     assert np.max(np.abs(out["lam"] - lam_ref)) <= tol * normA
     V = out["V"]
-    # convergence test of Sec. 4: ||r|| <= tau_c ||A|| with ||A|| estimated at set-up
+    # convergence test of Sec. 4, ||r|| <= tau_c ||A||, against the true ||A||:
+    # the solver locks against a lower bound of it (Lanczos Ritz values)
     norm_est = out["stats"]["norm_a"]
-    assert norm_est >= normA * (1 - 1e-12)
+    assert 0.5 * normA <= norm_est <= normA * (1 + 1e-12)
     res = np.linalg.norm(As @ V - V * out["lam"], axis=0)
-    assert res.max() <= tol * norm_est * (1 + 1e-6), res.max() / norm_est
+    assert res.max() <= tol * normA, res.max() / normA
     assert np.max(np.abs(V.conj().T @ V - np.eye(V.shape[1]))) < 1e-10
     assert np.max(np.abs(out["res"] - res / norm_est)) < 1e-12
 

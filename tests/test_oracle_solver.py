@@ -136,14 +136,16 @@ def _interval_around(lam, centre, cnt):
 def _check_result(r, As, lam_ref, normA_tol=1e-10):
     assert r.status == "ok"
     assert r.eigvals.size == lam_ref.size
-    normA = max(abs(lam_ref[0]), 1.0)
     lam_all = np.abs(np.linalg.eigvalsh(As.toarray())).max()
     assert np.max(np.abs(r.eigvals - lam_ref)) <= 1e-10 * lam_all
+    # the lock threshold's ||A|| never exceeds the spectral radius, so the
+    # residuals meet the Sec. 4 test against the true ||A||
+    normA = r.stats["setup"]["normA"]
+    assert 0.5 * lam_all <= normA <= lam_all * (1 + 1e-12)
     V = r.eigvecs
     res = np.linalg.norm(As @ V - V * r.eigvals, axis=0) / lam_all
-    assert np.all(res <= normA_tol * 1.5)
+    assert np.all(res <= normA_tol)
     assert np.max(np.abs(V.conj().T @ V - np.eye(V.shape[1]))) < 1e-10
-    del normA
 
 
 @pytest.mark.slow
@@ -197,3 +199,32 @@ def test_spurious_rule_ends_stall():
     assert any(h["e"] > 4 for h in r.stats["history"])   # a spurious value was present
     r2 = fsi.adapolysi(As, -0.1, 0.1, fsi.Params(**P, spurious_rule=False), V0, v0)
     assert r2.status == "no_convergence" and r2.stats["iterations"] == 30
+
+
+def test_shifted_cholqr_branch_runs_with_the_published_shift(monkeypatch):
+    """At kappa = 1e12 the Gram matrix's Cholesky factorisation breaks down
+    (kappa^2 > 1/u), so CholQR2 must take the shifted first pass of Fukaya et
+    al. (2020).  The shift is 11 (n p + p (p + 1)) u ||X||_F^2: R^H R - X^H X
+    equals s I up to rounding, so a shift ten times too large (or too small)
+    fails here."""
+    n, p = 500, 12
+    G = rng.uniform_block(3, rng.STREAM_TEST, n, p, True)
+    Q0, _ = np.linalg.qr(G)
+    U, _ = np.linalg.qr(rng.uniform_block(4, rng.STREAM_TEST, p, p, True))
+    # singular values down to 1e-12, with the last one exactly zero in the
+    # Gram matrix's precision: plain Cholesky cannot succeed
+    X = Q0 @ np.diag(np.concatenate([np.logspace(0, -12, p - 1), [1e-17]])) @ U
+    with pytest.raises(np.linalg.LinAlgError):
+        fsi.cholqr(X)
+    calls = []
+    orig = fsi.shifted_cholqr
+    monkeypatch.setattr(fsi, "shifted_cholqr", lambda Z: calls.append(1) or orig(Z))
+    Q = fsi.cholqr2(X)
+    assert calls == [1]
+    assert np.max(np.abs(Q.conj().T @ Q - np.eye(p))) < 1e-12
+    _, R = orig(X)
+    u = np.finfo(np.float64).eps / 2
+    s = 11.0 * (n * p + p * (p + 1)) * u * np.linalg.norm(X) ** 2
+    D = R.conj().T @ R - X.conj().T @ X
+    assert np.max(np.abs(D - s * np.eye(p))) <= 0.05 * s
+    assert np.allclose(np.real(np.diag(D)), s, rtol=0.05)

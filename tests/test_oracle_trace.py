@@ -93,3 +93,28 @@ def test_subspace_size_rule():
     assert trace.subspace_size(-3.0, 1.8, 1000, 1024) == 2    # floored at e~ = 1
     assert trace.subspace_size(900.0, 1.8, 1000, 1024) == 1000
     assert trace.subspace_size(900.0, 1.8, 5000, 1024) == 1024
+
+
+def test_moments_give_the_trace_estimate_and_the_exact_trace():
+    """sum_j a_j mu_j is the same Hutchinson estimate as trace_estimate (same
+    probes), and with the identity as the probe block it is the exact trace
+    sum_i rho(l(lambda_i)) from a dense eigendecomposition."""
+    import numpy as np
+    from oracle import chebyshev as cb
+    from oracle import fsi, trace
+    from synth import matrices, rng
+    A = matrices.anderson(7, 3, 3.0, 5, True)
+    As = A.to_scipy()
+    lmin, lmax = fsi.gershgorin(As)
+    l1, l2 = cb.linear_map(lmin, lmax)
+    k = 120
+    coef = cb.filter_coefficients(l1 * -0.4 + l2, l1 * 0.9 + l2, k)
+    Z = rng.rademacher_block(3, rng.STREAM_TEST, A.n, 8)
+    mu = trace.chebyshev_trace_moments(As, l1, l2, Z, k)
+    assert abs(coef @ mu - trace.trace_estimate(As, coef, l1, l2, Z)) < 1e-9 * A.n
+    mu_exact = trace.chebyshev_trace_moments(As, l1, l2, np.eye(A.n), k) * A.n
+    lam = np.linalg.eigvalsh(A.to_dense())
+    th = np.arccos(np.clip(l1 * lam + l2, -1, 1))
+    for j in (0, 1, 2, 17, k):
+        assert abs(mu_exact[j] - np.sum(np.cos(j * th))) < 1e-8 * A.n
+    assert abs(coef @ mu_exact - np.sum(cb.cheb_direct(coef, l1 * lam + l2))) < 1e-8 * A.n
