@@ -1610,7 +1610,7 @@ void residual_norms_public(apf_ctx* ctx, const apf_matrix* A, const T* V, int64_
 // that into APF_ERR_TIMEOUT.
 void wait_probe_pair(apf_ctx* ctx, const apf_matrix* A) {
   APF_REQUIRE(A->sell_ok, APF_ERR_ARG);
-  const int G = 32, VPT = 1;
+  const int G = 8, VPT = 1;  // a compiled shape (kSellShapes)
   const int R = 256 / G;
   APF_REQUIRE((int64_t)R * 4 < A->n, APF_ERR_ARG);
   const int64_t n = A->n, ld = 8;

@@ -114,6 +114,18 @@ def anderson3d_c_40() -> Workload:
 
 _BUILDERS["anderson3d_c_40"] = lambda seed: matrices.anderson(40, 3, 4.0, seed, complex_phases=True)
 
+def ks8_96() -> Workload:
+    """Real symmetric Kohn-Sham-like Hamiltonian on a 96^3 periodic grid
+    (n = 884,736): -1/2 times the eighth-order Laplacian (25 nonzeros per row)
+    plus 64 negative Gaussian wells (sigma = 1.5 grid units, seeded centres).
+    Interval [E_300, E_500] from the oracle's count estimate (stored in
+    tests/golden): about 200 eigenvalues around the midpoint of the
+    300th-500th; p = 300."""
+    a, b = _golden_interval("ks8_96")
+    return Workload("ks8_96", BASE_SEED + 2, 300, a, b, False,
+                    "Kohn-Sham-like 96^3 periodic, 8th-order stencil + 64 Gaussian wells, real, p=300")
+
+
 @dataclass
 class SliceWorkload:
     """Several disjoint intervals of one matrix (spectrum slicing)."""
@@ -152,6 +164,7 @@ WORKLOADS = {
     "anderson3d_c_64": anderson3d_c_64,
     "anderson3d_c_48": anderson3d_c_48,
     "anderson3d_c_40": anderson3d_c_40,
+    "ks8_96": ks8_96,
 }
 
 SLICE_WORKLOADS = {

@@ -45,3 +45,25 @@ def test_lap2d_interval_holds_its_stored_eigenvalues():
     lam = np.linalg.eigvalsh(A.to_dense())
     inside = lam[(lam >= w.a) & (lam <= w.b)]
     assert inside.size == 18
+
+
+def test_ks96_interval_agrees_with_the_weyl_count():
+    """The stored interval of the 96^3 Kohn-Sham-like workload (from the
+    oracle's count estimate) against an independent closed form: away from
+    the wells' bound states, -1/2 Laplacian on a periodic box of volume V has
+    N(E) ~ V (2E)^(3/2) / (6 pi^2) states below E (Weyl's law for a free
+    particle), so [a, b] should hold about N(b) - N(a) eigenvalues.  The wells
+    add a few per cent; the estimate said 200."""
+    import json
+    import os
+    w = workloads.ks8_96()
+    assert w.p == 300 and 0.0 < w.a < w.b
+    vol = 96.0 ** 3
+    weyl = lambda E: vol * (2.0 * E) ** 1.5 / (6.0 * np.pi ** 2)  # noqa: E731
+    est = weyl(w.b) - weyl(w.a)
+    assert 0.8 * 200 <= est <= 1.1 * 200, est
+    with open(os.path.join(os.path.dirname(__file__), "golden", "interval_ks8_96.json")) as f:
+        d = json.load(f)
+    assert abs(d["count_estimate"] - 200.0) < 1.0
+    # the bound states of 64 wells of depth 1 sit below zero, a handful per well
+    assert 20 <= d["count_below_zero"] <= 64 * 4
