@@ -288,9 +288,13 @@ def ours_arm(args, dist):
     iters = 0
     maxres = 0.0
     p_stat = deg_seq = None
+    stage = {"setup": 0.0, "filter": 0.0, "orth_rr": 0.0, "check": 0.0, "total": 0.0}
     for _ in range(args.steps):
         e, st, hist = one_solve()
         p_stat = st["p_used"]
+        for k_, s_ in (("setup", "ms_setup"), ("filter", "ms_filter"), ("orth_rr", "ms_rr"), ("check", "ms_check"),
+                       ("total", "ms_total")):
+            stage[k_] += st[s_] / args.steps
         deg_seq = [int(h["degree"]) for h in hist]
         eig += e
         fbytes += st["filter_bytes"]
@@ -368,6 +372,7 @@ def ours_arm(args, dist):
                    "precision": args.precision, "eigenpairs_per_solve": eig / args.steps,
                    "iterations_per_solve": iters / args.steps, "max_residual": maxres,
                    "p_used": p_stat, "degree_sequence": deg_seq,
+                   "stage_ms_per_solve": {k_: round(v_, 1) for k_, v_ in stage.items()},
                    "l2": f"inputs larger than L2 (FP32 block {blk_mb:.0f} MB, FP64 block {2 * blk_mb:.0f} MB)",
                    "parallelism": f"replicas{args.gpus}"},
         "roofline": {"kernel": f"Clenshaw filter step ({bits} {kind}, SELL-8)", "bound": "hbm",
