@@ -126,6 +126,8 @@ typedef struct {
 } apf_stats;
 
 #define APF_MAX_P 1024
+/* largest total subspace size of a batched solve (apf_solve_slices) */
+#define APF_MAX_SUM_P 8192
 
 /* ---- context --------------------------------------------------------- */
 
@@ -190,10 +192,12 @@ apf_status apf_matrix_destroy(apf_matrix* A);
  * variant does the same operations in the same order, so the choice changes
  * the time, never the result.  Pin one instead: kind 1 = SELL-8, one step per
  * launch; 2 = SELL-8, two steps per pass over a banded (reverse Cuthill-McKee)
- * copy; 3 = CSR.  (G, VPT) = lanes per row x 16-byte vectors per lane, (0, 0)
- * for the shape with the fewest idle lanes.  Where a pinned kind does not
- * apply (matrix, width) it falls back 2 -> 1 -> 3.  APF_ERR_ARG for a kind
- * outside 0..3. */
+ * copy; 3 = CSR; 4 = SELL-8 with the block cut into column tiles of G x VPT
+ * vectors, one tile per CTA, swept tile after tile (any width; the tile width
+ * is what keeps the far neighbours' rows of W in L2).  (G, VPT) = lanes per
+ * row x 16-byte vectors per lane, (0, 0) for the shape with the fewest idle
+ * lanes.  Where a pinned kind does not apply (matrix, width) it falls back
+ * 4 -> 1, 2 -> 1 -> 3.  APF_ERR_ARG for a kind outside 0..4. */
 apf_status apf_matrix_set_filter_kernel(apf_matrix* A, int32_t kind, int32_t G, int32_t VPT);
 apf_status apf_matrix_info(const apf_matrix* A, int64_t* n, int64_t* nnz, int32_t* dtype);
 
@@ -216,7 +220,8 @@ apf_status apf_solve(apf_ctx* ctx, const apf_matrix* A, const apf_params* params
  * `params` supplies every other setting (its a, b and p are ignored; its
  * init_block must be NULL: slice s starts from the seeded random block of
  * stream 1 + s).  The intervals must be pairwise disjoint, 1 <= p[s], and
- * sum(p) <= min(n, APF_MAX_P); else APF_ERR_ARG.  The result holds the union
+ * p[s] <= APF_MAX_P and sum(p) <= min(n, APF_MAX_SUM_P); else APF_ERR_ARG.
+ * The result holds the union
  * of the slices' pairs in ascending order of eigenvalue;
  * apf_result_slice_counts gives the count per slice (in input order).
  * APF_ERR_NO_CONVERGENCE if any slice reaches max_iter (partial result). */

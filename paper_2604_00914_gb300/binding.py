@@ -38,6 +38,7 @@ APF_FILTER_F32 = 1
 APF_FILTER_F32_DEFECT = 2
 
 APF_MAX_P = 1024
+APF_MAX_SUM_P = 8192
 
 HISTORY_FIELDS = ("degree", "width", "e", "locked", "n_lock", "max_res_in")
 

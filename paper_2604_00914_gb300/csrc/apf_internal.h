@@ -148,6 +148,15 @@ void clenshaw_step_sell(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* 
                         const typename ScalarTraits<T>::Real* coef_col,
                         typename ScalarTraits<T>::Real coef_scalar,
                         typename ScalarTraits<T>::Real alpha, T* Out);
+// The same step with the block cut into column tiles of G x VPT vectors, one
+// tile per CTA (grid: row ranges x tiles); any width.  See spmm_sell_ct.cuh.
+template <class T, class TA>
+void clenshaw_step_sell_ct(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* chunk_ptr,
+                           const int32_t* scol, const TA* sval, int lmax, const T* W, const T* Vin,
+                           const T* Y, int64_t ld, int64_t ncols,
+                           const typename ScalarTraits<T>::Real* coef_col,
+                           typename ScalarTraits<T>::Real coef_scalar,
+                           typename ScalarTraits<T>::Real alpha, T* Out);
 // Two consecutive Clenshaw steps in one pass (SELL-8, temporal blocking):
 // bufB = 2 A W - va + f1 Y with W = bufA, then bufA = 2 A bufB - bufA + f2 Y.
 // bandwidth: max |i - j| of the stored pattern; seg_count / pass: see spmm_sell.cuh.

@@ -576,7 +576,7 @@ apf_status apf_result_slice_counts(const apf_result* r, int32_t nslices, int64_t
 }
 
 apf_status apf_matrix_set_filter_kernel(apf_matrix* A, int32_t kind, int32_t G, int32_t VPT) {
-  if (!A || kind < 0 || kind > 3 || G < 0 || VPT < 0) return APF_ERR_ARG;
+  if (!A || kind < 0 || kind > 4 || G < 0 || VPT < 0) return APF_ERR_ARG;
   A->pin_kind = kind;
   A->pin_G = G;
   A->pin_VPT = VPT;

@@ -1,7 +1,7 @@
 // FP32 instantiations of the Clenshaw step (real and complex), the filter
 // recurrence of APF_FILTER_F32 / APF_FILTER_F32_DEFECT: the CSR kernel, the
 // SELL-8 kernel with TMA bulk staging, and the SELL value gather.
-#include "spmm_sell.cuh"
+#include "spmm_sell_ct.cuh"
 
 namespace apf {
 
@@ -48,6 +48,17 @@ void clenshaw_sell_pair(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* 
                                    ld, ncols, coef1_col, coef1, coef2_col, coef2, seg_count, pass);
 }
 
+template <class T, class TA>
+void clenshaw_step_sell_ct(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* chunk_ptr,
+                           const int32_t* scol, const TA* sval, int lmax, const T* W, const T* Vin,
+                           const T* Y, int64_t ld, int64_t ncols,
+                           const typename ScalarTraits<T>::Real* coef_col,
+                           typename ScalarTraits<T>::Real coef_scalar,
+                           typename ScalarTraits<T>::Real alpha, T* Out) {
+  clenshaw_sell_ct_launch<T, TA>(ctx, G, VPT, n, chunk_ptr, scol, sval, lmax, W, Vin, Y, ld, ncols, coef_col,
+                                 coef_scalar, alpha, Out);
+}
+
 template <class TA>
 __global__ void k_sell_gather(int64_t slots, const int32_t* __restrict__ src, const TA* __restrict__ csr,
                               TA* __restrict__ out) {
@@ -74,6 +85,9 @@ void sell_gather_values(apf_ctx* ctx, int64_t slots, const int32_t* src, const T
   template void clenshaw_step_sell<T, T>(apf_ctx*, int, int, int64_t, const int64_t*, const int32_t*, \
                                          const T*, int, const T*, const T*, const T*, int64_t,        \
                                          int64_t, const float*, float, float, T*);                    \
+  template void clenshaw_step_sell_ct<T, T>(apf_ctx*, int, int, int64_t, const int64_t*, const int32_t*, \
+                                            const T*, int, const T*, const T*, const T*, int64_t,        \
+                                            int64_t, const float*, float, float, T*);                    \
   template void sell_gather_values<T>(apf_ctx*, int64_t, const int32_t*, const T*, T*);              \
   template void clenshaw_sell_pair<T, T>(apf_ctx*, int, int, int64_t, const int64_t*, const int32_t*, \
                                          const T*, int, int64_t, T*, T*, const T*, const T*, int64_t, \

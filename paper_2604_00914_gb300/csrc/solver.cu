@@ -15,7 +15,7 @@
 
 #include "host_math.h"
 #include "solver.h"
-#include "spmm_sell.cuh"
+#include "spmm_sell_ct.cuh"
 
 namespace apf {
 
@@ -135,7 +135,9 @@ struct Stepper {
   const S* psell_vals = nullptr;  // A_hat values in permuted SELL-8 order, or null
   size_t seg_bytes = 0;
   int64_t ld = 0;
-  int kind = 0, G = 0, VPT = 0;  // kind 1: SELL, one step per launch; 2: SELL, two steps per launch
+  // kind 1: SELL, one step per launch; 2: SELL, two steps per launch; 4: SELL,
+  // one column tile of G x VPT vectors per CTA (any width); 0: CSR
+  int kind = 0, G = 0, VPT = 0;
   unsigned* seg_count = nullptr;  // pair-pass counters (kind 2)
   unsigned* pass = nullptr;       // passes made with seg_count
   bool pairs() const { return kind == 2; }
@@ -156,7 +158,11 @@ struct Stepper {
   }
   void operator()(const S* W, const S* Vin, const S* Y, int64_t ncols, const Real* coef_col,
                   Real coef_scalar, Real alpha, S* Out) const {
-    if (kind >= 1) {
+    if (kind == 4) {
+      if constexpr (sizeof(Real) == 4)
+        clenshaw_step_sell_ct<S, S>(ctx, G, VPT, A->n, A->sell_chunk_ptr, A->sell_col, sell_vals, A->sell_lmax, W,
+                                    Vin, Y, ld, ncols, coef_col, coef_scalar, alpha, Out);
+    } else if (kind >= 1) {
       // the two-step form keeps its blocks in the permuted row order: its
       // single steps (the last one or two) must use the permuted copy too
       if constexpr (sizeof(Real) == 4) {
@@ -179,6 +185,22 @@ struct Stepper {
 };
 
 constexpr int kNumSellShapes = (int)(sizeof(kSellShapes) / sizeof(kSellShapes[0]));
+constexpr int kNumSellCtShapes = (int)(sizeof(kSellCtShapes) / sizeof(kSellCtShapes[0]));
+
+// a column-tiled shape applies when its shared memory fits and the grid's
+// tile dimension stays within range
+template <class S>
+static bool sell_ct_fits(const Stepper<S>& st, int G, int VPT, int nvec) {
+  const int TV = G * VPT;
+  return sell_ct_smem_bytes(256 / G, TV, st.A->sell_lmax, sizeof(S)) <= 160 * 1024 &&
+         (nvec + TV - 1) / TV <= 65535 && st.A->n <= INT32_MAX;
+}
+
+// idle fraction of the vector slots of the column tiles covering nvec vectors
+static double ct_idle(int G, int VPT, int nvec) {
+  const int TV = G * VPT, tiles = (nvec + TV - 1) / TV;
+  return (double)(tiles * TV - nvec) / (tiles * TV);
+}
 
 template <class S>
 static bool sell_shape_fits(const Stepper<S>& st, int G, int VPT, int nvec) {
@@ -197,6 +219,19 @@ template <class S>
 static void pinned_shape(Stepper<S>& st, int nvec) {
   const apf_matrix* A = st.A;
   int kind = A->pin_kind == 3 ? 0 : A->pin_kind;
+  if (kind == 4) {
+    if (A->sell_ok) {
+      int bg = 0, bv = 0;
+      for (int i = 0; i < kNumSellCtShapes; ++i) {
+        const int g = kSellCtShapes[i].G, v = kSellCtShapes[i].VPT;
+        if (!sell_ct_fits(st, g, v, nvec)) continue;
+        if (g == A->pin_G && v == A->pin_VPT) { bg = g; bv = v; break; }
+        if (bg == 0 || ct_idle(g, v, nvec) < ct_idle(bg, bv, nvec) - 1e-12) { bg = g; bv = v; }
+      }
+      if (bg) { st.kind = 4; st.G = bg; st.VPT = bv; return; }
+    }
+    kind = 1;
+  }
   if (kind >= 1 && !(A->sell_ok && nvec <= 256)) kind = 0;
   if (kind == 2) {
     const int R = 256 / (A->pin_G > 0 ? A->pin_G : 8);
@@ -282,6 +317,22 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
       const int64_t bwp = A->perm ? A->psell_bw : A->sell_bw;
       const double window = (double)(2 * bwp + (PAIR_SEG + 1) * R) * st.ld * sizeof(S) * 3.0;
       if (window <= 64.0 * 1024 * 1024 && (int64_t)R * 4 < A->n) cands.push_back({2, g, v});
+    }
+  }
+  if (A->sell_ok) {
+    // column tiles: the shapes with at most 25 % idle slots, or the least idle one
+    int least = -1;
+    for (int i = 0; i < kNumSellCtShapes; ++i) {
+      const int g = kSellCtShapes[i].G, v = kSellCtShapes[i].VPT;
+      if (!sell_ct_fits(st, g, v, nvec)) continue;
+      if (least < 0 || ct_idle(g, v, nvec) < ct_idle(kSellCtShapes[least].G, kSellCtShapes[least].VPT, nvec))
+        least = i;
+    }
+    for (int i = 0; i < kNumSellCtShapes; ++i) {
+      const int g = kSellCtShapes[i].G, v = kSellCtShapes[i].VPT;
+      if (!sell_ct_fits(st, g, v, nvec)) continue;
+      if (ct_idle(g, v, nvec) > 0.25 && i != least) continue;
+      cands.push_back({4, g, v});
     }
   }
   APF_REQUIRE(!cands.empty(), APF_ERR_ARG);
@@ -1365,7 +1416,7 @@ static void solve_slices_t(apf_ctx* ctx, const apf_matrix* A, int ns, const doub
     ptot += ps[(size_t)s];
     pmax = std::max(pmax, ps[(size_t)s]);
   }
-  APF_REQUIRE(ptot <= n && ptot <= APF_MAX_P, APF_ERR_ARG);
+  APF_REQUIRE(ptot <= n && ptot <= APF_MAX_SUM_P, APF_ERR_ARG);
   st.p_used = ptot;
   SmallWork<T> sw;
   sw.init(pmax, ctx->stream);

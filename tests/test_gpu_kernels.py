@@ -1,6 +1,7 @@
 """Every compiled variant of the FP32 Clenshaw step (Alg. 2) gives the same
 bits: SELL-8 one step per launch in each (G, VPT) shape, SELL-8 two steps per
-pass over the reverse Cuthill-McKee copy, and CSR.  The autotuner picks among
+pass over the reverse Cuthill-McKee copy, SELL-8 in column tiles of each
+compiled tile width (also on blocks wider than 1024 columns), and CSR.  The autotuner picks among
 them by time, so a result must not depend on the pick (a serving request gives
 the same answer alone and in a mix).  Matrices with a wide natural bandwidth
 (periodic lattices) get the permuted copy; small ones stay in natural order.
@@ -18,6 +19,7 @@ pytestmark = pytest.mark.gpu
 
 SELL_SHAPES = [(8, 1), (8, 2), (8, 3), (8, 4), (16, 2), (16, 3), (16, 4), (16, 5), (16, 6),
                (32, 2), (32, 3), (32, 4), (32, 5), (32, 6), (32, 8)]
+CT_SHAPES = [(8, 1), (8, 2), (16, 1), (8, 4), (16, 2), (32, 1), (16, 4), (32, 2)]
 
 MATS = [
     ("lap2d_32", lambda: workloads.lap2d_32().matrix()),                      # natural order
@@ -45,6 +47,7 @@ def _variants(p, is_complex):
     out = [(3, 0, 0)]
     for kind in (1, 2):
         out += [(kind, g, v) for g, v in SELL_SHAPES if g * v >= nvec]
+    out += [(4, g, v) for g, v in CT_SHAPES]
     return out
 
 
@@ -88,7 +91,7 @@ def test_defect_form_agrees_across_kernels(B, ctx, name, make):
     lam = np.real(np.sum(V.conj() * AV, axis=0))
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
     outs = []
-    for kind, g, v in [(3, 0, 0), (1, 0, 0), (2, 0, 0), (2, 16, 2), (1, 32, 4)]:
+    for kind, g, v in [(3, 0, 0), (1, 0, 0), (2, 0, 0), (2, 16, 2), (1, 32, 4), (4, 8, 2), (4, 32, 2)]:
         M.set_filter_kernel(kind, g, v)
         Y = empty_like_np((A.n, p), A.is_complex)
         B.filter_apply_defect(ctx, M, coef, l1, l2, dev(V), dev(AV), dev(lam), Y)
@@ -110,7 +113,7 @@ def test_solve_is_the_same_with_every_pinned_kernel(B, ctx):
     a, b = 0.5 * (lam[i - 1] + lam[i]), 0.5 * (lam[i + c - 1] + lam[i + c])
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
     got = []
-    for kind in (0, 1, 2, 3):
+    for kind in (0, 1, 2, 3, 4):
         M.set_filter_kernel(kind)
         r = B.solve(ctx, M, B.default_params(a=a, b=b, p=24, seed=3, filter_precision=B.APF_FILTER_F32_DEFECT))
         got.append(r.eigvals())
@@ -124,8 +127,34 @@ def test_solve_is_the_same_with_every_pinned_kernel(B, ctx):
 def test_set_filter_kernel_rejects_bad_kind(B, ctx):
     A = matrices.anderson(5, 3, 4.0, 3, False)
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
-    for kind in (-1, 4):
+    for kind in (-1, 5):
         with pytest.raises(B.ApfError) as ei:
             M.set_filter_kernel(kind)
         assert ei.value.status == B.APF_ERR_ARG
     M.close()
+
+
+@pytest.mark.parametrize("is_complex", [False, True])
+def test_column_tiles_on_wide_blocks(B, ctx, is_complex):
+    """Blocks wider than one thread group covers (1100 real / 700 complex
+    columns): the column-tiled SELL kernel in every tile width against the CSR
+    kernel (column slabs) bit for bit, and against the oracle."""
+    A = matrices.anderson(12, 3, 3.0, 8, is_complex)
+    As = A.to_scipy()
+    p = 700 if is_complex else 1100
+    lmin, lmax = fsi.gershgorin(As)
+    l1, l2 = cb.linear_map(lmin, lmax)
+    coef = cb.filter_coefficients(-0.3, 0.1, 33)
+    X = rng.uniform_block(13, rng.STREAM_TEST, A.n, p, is_complex)
+    ref = clenshaw_apply(As, coef, l1, l2, X)
+    M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
+    outs = []
+    for kind, g, v in [(3, 0, 0)] + [(4, g, v) for g, v in CT_SHAPES]:
+        M.set_filter_kernel(kind, g, v)
+        Y = empty_like_np((A.n, p), is_complex)
+        B.filter_apply(ctx, M, coef, l1, l2, dev(X), Y, B.APF_FILTER_F32)
+        outs.append(host(Y))
+    M.close()
+    assert np.max(np.abs(outs[0] - ref)) <= clenshaw_tol(coef, X, EPS32)
+    for y in outs[1:]:
+        assert np.array_equal(outs[0], y)
