@@ -358,18 +358,32 @@ apf_status apf_gram(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t 
                     const void* X, int64_t ldx, const void* Y, int64_t ldy,
                     void* G, int64_t ldg);
 
-/* The same G = X^H Y as apf_gram, to FP64 accuracy, on the bf16 tensor cores:
- * each column is split into 7 signed 8-bit slices under a per-column power of
- * two (the Ozaki scheme), the slice products accumulate exactly in FP32 over
- * 64-row chunks and are carried in FP64.  The error is at most about
- * n 2^(e_a + e_b - 53), where 2^e_a (< twice column a's largest entry)
- * bounds column a: within a small factor of an FP64 product's worst case
- * for columns whose entries are of one size.
- * Same arguments and errors as apf_gram; pa, pb <= APF_MAX_P.  Allocates the
- * slices (7 x 2 x n x pa bf16 for complex X) for the call. */
+/* The same G = X^H Y as apf_gram, to FP64 accuracy, on the tcgen05 tensor
+ * cores (bf16 in, FP32 accumulate): each column is split into seven balanced
+ * 8-bit digits of round(x 2^(55 - e_a)) under a per-column power of two 2^e_a
+ * (the Ozaki scheme); the digit products of each diagonal s + t = d <= 6
+ * accumulate exactly in FP32 over 32-row chunks and are carried exactly in
+ * 64-bit integers.  The error is at most about n 2^(e_a + e_b - 55), where
+ * 2^e_a (< twice column a's largest entry) bounds column a: within a small
+ * factor of an FP64 product's worst case.  Same arguments and errors as
+ * apf_gram (APF_ERR_TIMEOUT if a device wait gave up); pa, pb <= APF_MAX_P.
+ * The digits (7 x n x pa bf16, twice for complex) live in a workspace of the
+ * context that grows to the largest call and is kept until apf_destroy. */
 apf_status apf_gram_tc(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t pb,
                        const void* X, int64_t ldx, const void* Y, int64_t ldy,
                        void* G, int64_t ldg);
+
+/* Z = beta Z + alpha X M: the tall block products of Alg. 4 (X R^{-1} in
+ * Cholesky QR, the Ritz vectors Q U of Rayleigh-Ritz, the projection
+ * X - V (V^H X) against the locked vectors).  X: n x pa, M: pa x pb, Z: n x pb,
+ * all device, row-major, of `dtype`; Z must not overlap X or M.
+ * tensor_cores = 0: FP64 cores; 1: the tcgen05 tensor cores with the same
+ * digit slicing as apf_gram_tc (each row of X and each column of M under its
+ * own power of two, seven 8-bit digits, exact integer carry), to FP64
+ * accuracy relative to the row and column maxima.  pa, pb <= APF_MAX_P. */
+apf_status apf_block_update(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t pb, const void* X,
+                            int64_t ldx, const void* M, int64_t ldm, void* Z, int64_t ldz, double alpha,
+                            double beta, int32_t tensor_cores);
 
 /* Orthogonalisation of Alg. 4: X (device n x p) is replaced by Q with X = Q R, by CholQR2
  * (shifted CholQR3 when the first factorisation breaks down). */

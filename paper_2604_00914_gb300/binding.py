@@ -152,6 +152,7 @@ SIGNATURES = {
     "apf_gram": (_I32, [_P, _I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64]),
     "apf_gram_tc": (_I32, [_P, _I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64]),
     "apf_cholqr2": (_I32, [_P, _I32, _I64, _I64, _P, _I64]),
+    "apf_block_update": (_I32, [_P, _I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _D, _D, _I32]),
     "apf_eigh_small": (_I32, [_P, _I32, _I64, _P, _I64, _P, _P, _I64]),
     "apf_rayleigh_ritz": (_I32, [_P, _P, _P, _I64, _I64, _P, _P, _I64]),
     "apf_residual_norms": (_I32, [_P, _P, _P, _I64, _I64, _P, _P]),
@@ -545,6 +546,17 @@ def gram_tc(ctx, X, Y, G):
     ctx.lib.check(ctx.lib.apf_gram_tc(ctx.h, dt, n, pa, pb, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
                                       _ptr(G), G.stride(0)), ctx.h)
     return G
+
+
+def block_update(ctx, X, M, Z, alpha=1.0, beta=0.0, tensor_cores=True):
+    """apf_block_update: Z = beta Z + alpha X M on device tensors."""
+    n, pa = X.shape
+    pb = M.shape[1]
+    dt = APF_C128 if X.is_complex() else APF_R64
+    ctx.lib.check(ctx.lib.apf_block_update(ctx.h, dt, n, pa, pb, _ptr(X), X.stride(0), _ptr(M), M.stride(0),
+                                           _ptr(Z), Z.stride(0), float(alpha), float(beta),
+                                           1 if tensor_cores else 0), ctx.h)
+    return Z
 
 
 def cholqr2(ctx, X):

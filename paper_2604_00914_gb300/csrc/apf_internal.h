@@ -51,6 +51,8 @@ struct apf_ctx {
   double* h_pinned = nullptr;    // pinned staging buffer
   size_t h_pinned_bytes = 0;
   uint64_t wait_limit_ns = 0;    // device-side wait limit (apf_set_wait_limit); 0: the defaults below
+  void* ws = nullptr;            // workspace of the tensor-core products (grown on demand)
+  size_t ws_bytes = 0;
   std::string last_error;
 };
 
@@ -204,6 +206,10 @@ void gram_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_
 template <class T>
 void gram(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_t ldx,
           const T* Y, int64_t ldy, T* G, int64_t ldg, bool hermitian);
+// Z = beta Z0 + alpha X M on the tensor cores, FP64-accurate (k_oz_tc.cu)
+template <class T>
+void gemm_tall_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_t ldx, const T* M,
+                  int64_t ldm, T* Z, int64_t ldz, double alpha, double beta, const T* Z0, int64_t ldz0);
 
 // gram() with the split partials in caller-provided device scratch (no allocation)
 template <class T>

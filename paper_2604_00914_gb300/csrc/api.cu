@@ -84,6 +84,7 @@ apf_status apf_destroy(apf_ctx* ctx) {
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->d_bar) cudaFree(ctx->d_bar);
   if (ctx->d_counters) cudaFree(ctx->d_counters);
+  if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return APF_OK;
@@ -764,6 +765,39 @@ apf_status apf_gram_tc(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64
     apf::gram_tc<double>(ctx, n, pa, pb, static_cast<const double*>(X), ldx, static_cast<const double*>(Y), ldy,
                          static_cast<double*>(G), ldg, false);
   APF_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (apf::fetch_device_error(ctx) != 0) throw ApfError{APF_ERR_TIMEOUT, "tensor-core Gram"};
+  APF_CATCH(ctx)
+}
+
+apf_status apf_block_update(apf_ctx* ctx, int32_t dtype, int64_t n, int64_t pa, int64_t pb, const void* X,
+                            int64_t ldx, const void* M, int64_t ldm, void* Z, int64_t ldz, double alpha, double beta,
+                            int32_t tensor_cores) {
+  if (!ctx || !X || !M || !Z || n < 1 || pa < 1 || pb < 1 || pa > APF_MAX_P || pb > APF_MAX_P || ldx < pa ||
+      ldm < pb || ldz < pb)
+    return APF_ERR_ARG;
+  if (dtype != APF_R64 && dtype != APF_C128) return APF_ERR_ARG;
+  APF_TRY(ctx)
+  bind(ctx);
+  const double b = beta;
+  if (dtype == APF_C128) {
+    auto* z = static_cast<double2*>(Z);
+    if (tensor_cores)
+      apf::gemm_tall_tc<double2>(ctx, n, pa, pb, static_cast<const double2*>(X), ldx, static_cast<const double2*>(M),
+                                 ldm, z, ldz, alpha, b, b != 0.0 ? z : nullptr, ldz);
+    else
+      apf::gemm_tall<double2>(ctx, n, pa, pb, static_cast<const double2*>(X), ldx, static_cast<const double2*>(M),
+                              ldm, z, ldz, alpha, b, b != 0.0 ? z : nullptr, ldz, false);
+  } else {
+    auto* z = static_cast<double*>(Z);
+    if (tensor_cores)
+      apf::gemm_tall_tc<double>(ctx, n, pa, pb, static_cast<const double*>(X), ldx, static_cast<const double*>(M), ldm,
+                                z, ldz, alpha, b, b != 0.0 ? z : nullptr, ldz);
+    else
+      apf::gemm_tall<double>(ctx, n, pa, pb, static_cast<const double*>(X), ldx, static_cast<const double*>(M), ldm,
+                             z, ldz, alpha, b, b != 0.0 ? z : nullptr, ldz, false);
+  }
+  APF_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (apf::fetch_device_error(ctx) != 0) throw ApfError{APF_ERR_TIMEOUT, "block update"};
   APF_CATCH(ctx)
 }
 

@@ -894,6 +894,15 @@ static void gram_on(apf_ctx* ctx, bool tc, int64_t n, int64_t pa, int64_t pb, co
   else gram<T>(ctx, n, pa, pb, X, ldx, Y, ldy, G, ldg, hermitian);
 }
 
+// Z = beta Z0 + alpha X M on the FP64 cores or on the tensor cores.
+template <class T>
+static void gemm_on(apf_ctx* ctx, bool tc, int64_t n, int64_t pa, int64_t pb, const T* X, int64_t ldx, const T* M,
+                    int64_t ldm, T* Z, int64_t ldz, double alpha, double beta, const T* Z0, int64_t ldz0,
+                    bool upper) {
+  if (tc) gemm_tall_tc<T>(ctx, n, pa, pb, X, ldx, M, ldm, Z, ldz, alpha, beta, Z0, ldz0);
+  else gemm_tall<T>(ctx, n, pa, pb, X, ldx, M, ldm, Z, ldz, alpha, beta, Z0, ldz0, upper);
+}
+
 // One Cholesky QR pass Xout = X R^{-1}, R from G = X^H X (+ shift I).
 template <class T>
 static bool cholqr_pass(apf_ctx* ctx, int64_t n, int64_t p, const T* X, int64_t ld, T* Xout,
@@ -911,7 +920,7 @@ static bool cholqr_pass(apf_ctx* ctx, int64_t n, int64_t p, const T* X, int64_t 
   }
   if (!cholesky_checked<T>(ctx, p, sw.G, p, shift)) return false;
   tri_inv_upper<T>(ctx, p, sw.G, p, sw.Ri, p);
-  gemm_tall<T>(ctx, n, p, p, X, ld, sw.Ri, p, Xout, ld, 1.0, 0.0, nullptr, ld, true);
+  gemm_on<T>(ctx, tc, n, p, p, X, ld, sw.Ri, p, Xout, ld, 1.0, 0.0, nullptr, ld, true);
   return true;
 }
 
@@ -947,7 +956,7 @@ static void orth_rr(apf_ctx* ctx, const apf_matrix* A, int64_t p, int64_t ld, T*
   const int64_t n = A->n;
   for (int pass = 0; pass < 2 && nlock > 0; ++pass) {
     gram_on<T>(ctx, tc, n, nlock, p, Vlock, ldl, X, ld, sw.C, p, false);
-    gemm_tall<T>(ctx, n, nlock, p, Vlock, ldl, sw.C, p, X, ld, -1.0, 1.0, X, ld, false);
+    gemm_on<T>(ctx, tc, n, nlock, p, Vlock, ldl, sw.C, p, X, ld, -1.0, 1.0, X, ld, false);
   }
   if (!cholqr_pass<T>(ctx, n, p, X, ld, X1, sw, false, tc)) {
     if (!cholqr_pass<T>(ctx, n, p, X, ld, X1, sw, true, tc)) throw ApfError{APF_ERR_CHOL, "shifted CholQR"};
@@ -965,7 +974,7 @@ static void orth_rr(apf_ctx* ctx, const apf_matrix* A, int64_t p, int64_t ld, T*
   symmetrize<T>(ctx, p, sw.B, p);
   eigh_jacobi<T>(ctx, p, sw.B, p, w, sw.U, p);
   small_gemm<T>(ctx, p, p, p, 'N', sw.Ri, p, 'N', sw.U, p, sw.M, p, 1.0, 0.0);
-  gemm_tall<T>(ctx, n, p, p, X1, ld, sw.M, p, Vh, ld, 1.0, 0.0, nullptr, ld, false);
+  gemm_on<T>(ctx, tc, n, p, p, X1, ld, sw.M, p, Vh, ld, 1.0, 0.0, nullptr, ld, false);
   spmm_plain<T>(ctx, A, Vh, ld, p, AVh);
   residual_norms<T>(ctx, n, p, AVh, Vh, ld, w, res, nullptr, 0.0);
 }

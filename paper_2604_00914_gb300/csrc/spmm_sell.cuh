@@ -369,6 +369,16 @@ inline void allow_large_smem(int device) {
   done.fetch_or(bit, std::memory_order_release);
 }
 
+// The same for an explicit number of bytes.
+template <auto Kern>
+inline void allow_large_smem_bytes(int device, int bytes) {
+  static std::atomic<uint64_t> done{0};
+  const uint64_t bit = 1ull << (device & 63);
+  if (done.load(std::memory_order_acquire) & bit) return;
+  APF_CUDA(cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit, std::memory_order_release);
+}
+
 template <class T, class TA>
 void clenshaw_sell_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* chunk_ptr,
                           const int32_t* scol, const TA* sval, int lmax, const T* W, const T* Vin,

@@ -27,6 +27,18 @@ EncodeTiled encoder() {
 }
 }  // namespace
 
+bool encode_tmap(CUtensorMap* out, CUtensorMapDataType dtype, int rank, const void* base, const cuuint64_t* dims,
+                 const cuuint64_t* strides, const cuuint32_t* box, CUtensorMapSwizzle swizzle) {
+  EncodeTiled fn = encoder();
+  if (!fn || ((uintptr_t)base & 15u) || rank < 1 || rank > 5) return false;
+  for (int i = 0; i + 1 < rank; ++i)
+    if (strides[i] & 15u) return false;
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return fn(out, dtype, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dtype, const void* base, uint64_t inner,
                     uint64_t rows, uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_rows,
                     CUtensorMapSwizzle swizzle) {

@@ -14,5 +14,9 @@ namespace apf {
 bool encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dtype, const void* base, uint64_t inner,
                     uint64_t rows, uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_rows,
                     CUtensorMapSwizzle swizzle);
+// General tiled map of `rank` dimensions (innermost first); strides in bytes
+// for dimensions 1..rank-1, each a multiple of 16.
+bool encode_tmap(CUtensorMap* out, CUtensorMapDataType dtype, int rank, const void* base, const cuuint64_t* dims,
+                 const cuuint64_t* strides, const cuuint32_t* box, CUtensorMapSwizzle swizzle);
 
 }  // namespace apf

@@ -111,3 +111,25 @@ def test_gram_tc_rejects_bad_arguments(B, ctx):
     Gb = torch.zeros((1100, 1100), dtype=torch.float64, device="cuda")
     assert lib.apf_gram_tc(ctx.h, B.APF_R64, 2, 1100, 1100, big.data_ptr(), 1100, big.data_ptr(), 1100,
                            Gb.data_ptr(), 1100) == B.APF_ERR_ARG
+
+
+@pytest.mark.parametrize("is_complex", [False, True])
+@pytest.mark.parametrize("n,pa,pb", [(1000, 37, 45), (129, 1, 1), (3001, 160, 33), (20000, 300, 300),
+                                     (777, 200, 7)])
+def test_block_update_tc_matches_fp64(B, ctx, is_complex, n, pa, pb):
+    """Z = beta Z + alpha X M on the tensor cores against the FP64 cores and
+    numpy: rows of X and columns of M carry their own powers of two, so the
+    error is about pa 2^-55 max|x_i| max|m_j| per entry."""
+    X = rng.uniform_block(70 + pa, rng.STREAM_TEST, n, pa, is_complex) * np.logspace(-3, 3, n)[:, None]
+    M = rng.uniform_block(80 + pb, rng.STREAM_TEST, pa, pb, is_complex)
+    Z0 = rng.uniform_block(90, rng.STREAM_TEST, n, pb, is_complex)
+    for alpha, beta in ((1.0, 0.0), (-1.0, 1.0)):
+        ref = beta * Z0 + alpha * (X @ M)
+        Zt = dev(Z0.copy())
+        B.block_update(ctx, dev(X), dev(M), Zt, alpha, beta, tensor_cores=True)
+        Zf = dev(Z0.copy())
+        B.block_update(ctx, dev(X), dev(M), Zf, alpha, beta, tensor_cores=False)
+        scale = np.outer(np.max(np.abs(X), axis=1), np.max(np.abs(M), axis=0))
+        tol = 8.0 * pa * EPS64 * scale + 4 * EPS64 * np.abs(ref)
+        assert np.all(np.abs(host(Zt) - ref) <= tol)
+        assert np.all(np.abs(host(Zt) - host(Zf)) <= tol + 8.0 * pa * EPS64 * scale)

@@ -1,13 +1,16 @@
-"""The arithmetic behind the tensor-core Gram product (apf_gram_tc), modelled
-on the CPU: columns scaled by their own power of two and cut into seven
-signed 8-bit slices, products of slices summed exactly, diagonals s + t <= 6
-kept and carried in FP64.  Checked against exact rational arithmetic:
+"""The arithmetic behind the tensor-core products (apf_gram_tc,
+apf_block_update with tensor_cores = 1), modelled on the CPU and checked
+against exact rational arithmetic:
 
- - each slice is an integer in [-128, 128] (held exactly by bf16) and the
-   slices rebuild the value to within 2^(e - 56), exactly when the value is
-   within a factor 4 of the column's largest;
- - a 64-row chunk's sums stay below 2^24 (FP32 adds them exactly in any order);
- - the truncated product is within n 2^(e_a + e_b - 53) of the exact one.
+ - a value x with |x| < 2^E becomes F = round(x 2^(55 - E)), cut into seven
+   balanced base-256 digits in [-128, 128] (held exactly by bf16) that rebuild
+   F exactly, so x is represented to within 2^(E - 56);
+ - a 32-row chunk's digit-product sums on a diagonal stay below 2^22 (FP32
+   adds them exactly in any order, and the hi / lo carry of the kernel is
+   exact integer arithmetic);
+ - the carried sums give the product to within n 2^(E_a + E_b - 55);
+ - the digits the model computes equal a direct integer computation from the
+   bits of x (the kernel's method) on random, tiny, huge and signed values.
 """
 from fractions import Fraction
 
@@ -15,67 +18,114 @@ import numpy as np
 
 from synth import rng
 
-S, KC = 7, 64
+S, KC = 7, 32
 
 
-def _slices(x, e):
-    """The device split: t = x 2^-e, then sigma_0 = rint(128 t), sigma_s =
-    rint(256 rem) for s >= 1, in FP64."""
-    t = np.ldexp(x, -e)
-    out = []
-    for s in range(S):
-        v = t * (128.0 if s == 0 else 256.0)
-        sig = np.rint(v)
-        t = v - sig
-        out.append(sig)
-    return np.array(out)  # S x n
-
-
-def _exponent(col):
-    m = np.max(np.abs(col))
+def _exponent(v):
+    """E with max |v| < 2^E (0 for an all-zero vector)."""
+    m = np.max(np.abs(v))
     return int(np.frexp(m)[1]) if m > 0 else 0
 
 
-def test_slices_are_small_integers_and_rebuild_the_value():
+def _digits(x, E):
+    """Balanced base-256 digits of F = round(x 2^(55 - E)) (halves away from
+    zero), low digit last."""
+    t = abs(Fraction(float(x))) * Fraction(2) ** (55 - E)
+    F = int(t + Fraction(1, 2))  # floor(|t| + 1/2)
+    if x < 0:
+        F = -F
+    dg = [0] * S
+    for s in range(S - 1, 0, -1):
+        d = F & 0xFF
+        if d >= 128:
+            d -= 256
+        dg[s] = d
+        F = (F - d) >> 8
+    dg[0] = F
+    return dg
+
+
+def _digits_from_bits(x, E):
+    """The kernel's route: mantissa and exponent bits, integer shifts, round
+    half away from zero on the magnitude."""
+    b = int(np.array([x], dtype=np.float64).view(np.int64)[0])
+    ex = (b >> 52) & 0x7FF
+    F = 0
+    if ex:
+        m = (b & ((1 << 52) - 1)) | (1 << 52)
+        sh = ex - 1020 - E
+        if sh >= 0:
+            F = m << min(sh, 2)
+        elif sh > -62:
+            F = (m + (1 << (-sh - 1))) >> (-sh)
+    if b < 0:
+        F = -F
+    dg = [0] * S
+    for s in range(S - 1, 0, -1):
+        d = F & 0xFF
+        if d >= 128:
+            d -= 256
+        dg[s] = d
+        F = (F - d) >> 8
+    dg[0] = F
+    return dg
+
+
+def test_digits_are_small_integers_and_rebuild_the_value():
     x = rng.uniform_block(3, rng.STREAM_TEST, 500, 1, False)[:, 0] * 7.3
-    e = _exponent(x)
-    sl = _slices(x, e)
-    assert np.all(sl == np.rint(sl)) and np.max(np.abs(sl)) <= 128
+    E = _exponent(x)
     for i in range(0, 500, 7):
-        rebuilt = sum(Fraction(int(sl[s, i])) * Fraction(2) ** (e - 7 - 8 * s) for s in range(S))
-        err = abs(rebuilt - Fraction(float(x[i])))
-        assert err <= Fraction(2) ** (e - 56)
-        if abs(x[i]) >= 2.0 ** (e - 2):
-            assert err == 0
+        dg = _digits(x[i], E)
+        assert max(abs(d) for d in dg) <= 128
+        rebuilt = sum(Fraction(d) * Fraction(2) ** (E - 55 + 8 * (S - 1 - s)) for s, d in enumerate(dg))
+        assert abs(rebuilt - Fraction(float(x[i]))) <= Fraction(2) ** (E - 56)
 
 
-def test_chunk_sums_fit_fp32_exactly():
-    """Worst case: every slice at +-128, seven slice pairs on a diagonal, two
-    products per entry (real and imaginary combination), 64 rows."""
-    worst = S * 2 * KC * 128 * 128
-    assert worst < 2 ** 24
+def test_bit_route_equals_rational_route():
+    vals = list(rng.uniform_block(4, rng.STREAM_TEST, 300, 1, False)[:, 0] * 3.0)
+    vals += [0.0, -0.0, 1e-300, -1e-300, 2.0 ** -1074, 0.999999999, -0.5, 0.5, 1.5, -1.75]
+    # ties: x 2^53 has a fractional part of exactly 1/2 (rounded away from zero)
+    vals += [3 * 2.0 ** -54, -5 * 2.0 ** -54, (2 ** 50 + 1) * 2.0 ** -51 + 2.0 ** -54]
+    E = 2  # |values| < 4
+    for v in vals:
+        assert _digits_from_bits(v, E) == _digits(v, E), v
+    # the largest magnitude sits right below 2^E
+    big = np.nextafter(4.0, 0.0)
+    assert _digits_from_bits(big, E) == _digits(big, E)
+    assert _digits_from_bits(-big, E) == _digits(-big, E)
 
 
-def test_truncated_product_error_bound():
+def test_chunk_sums_fit_fp32_and_the_carry():
+    """Worst case: every digit at +-128, seven digit pairs on a diagonal, 32
+    rows: below 2^22.  Carry words: hi gains < 2^36 and lo < 2^46 per chunk, so
+    2^16 chunks (the kernel's limit) stay far inside 64 bits."""
+    worst = S * KC * 128 * 128
+    assert worst < 2 ** 22
+    hi = worst * (2 ** 16 + 2 ** 8 + 1)
+    lo = worst * (2 ** 24 + 2 ** 16 + 2 ** 8 + 1)
+    assert hi * 2 ** 16 < 2 ** 63 and lo * 2 ** 16 < 2 ** 63
+
+
+def test_carried_product_error_bound():
     n, pa, pb = 300, 3, 4
     X = rng.uniform_block(5, rng.STREAM_TEST, n, pa, False) * np.array([1e-3, 1.0, 40.0])
     Y = rng.uniform_block(6, rng.STREAM_TEST, n, pb, False) * np.array([2.0, 1e5, 0.5, 1e-7])
     ex = [_exponent(X[:, a]) for a in range(pa)]
     ey = [_exponent(Y[:, b]) for b in range(pb)]
-    SX = [_slices(X[:, a], ex[a]) for a in range(pa)]
-    SY = [_slices(Y[:, b], ey[b]) for b in range(pb)]
+    DX = [[_digits(X[i, a], ex[a]) for i in range(n)] for a in range(pa)]
+    DY = [[_digits(Y[i, b], ey[b]) for i in range(n)] for b in range(pb)]
     for a in range(pa):
         for b in range(pb):
-            acc = 0.0
-            for c0 in range(0, n, KC):  # chunks: exact integer sums, then the FP64 carry
+            hi = lo = 0
+            for c0 in range(0, n, KC):
+                P = [0] * S
                 for d in range(S):
-                    chunk = 0
                     for s in range(d + 1):
-                        chunk += int(np.dot(SX[a][s, c0:c0 + KC].astype(np.int64),
-                                            SY[b][d - s, c0:c0 + KC].astype(np.int64)))
-                    assert abs(chunk) < 2 ** 24
-                    acc += float(chunk) * 2.0 ** (-8 * d)
-            got = np.ldexp(acc, ex[a] + ey[b] - 14)
+                        P[d] += sum(DX[a][i][s] * DY[b][i][d - s] for i in range(c0, min(n, c0 + KC)))
+                    assert abs(P[d]) < 2 ** 22
+                hi += (P[0] << 16) + (P[1] << 8) + P[2]
+                lo += (P[3] << 24) + (P[4] << 16) + (P[5] << 8) + P[6]
+            got = Fraction(hi * 2 ** 32 + lo) * Fraction(2) ** (ex[a] + ey[b] - 62)
             exact = sum(Fraction(float(X[i, a])) * Fraction(float(Y[i, b])) for i in range(n))
-            bound = n * Fraction(2) ** (ex[a] + ey[b] - 53)
-            assert abs(Fraction(got) - exact) <= bound, (a, b)
+            bound = n * Fraction(2) ** (ex[a] + ey[b] - 55)
+            assert abs(got - exact) <= bound, (a, b)
