@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--filter-only", type=int, default=0,
                     help="time only N applications of the filter kernel (degree --degree) instead of solves")
     ap.add_argument("--degree", type=int, default=20)
+    ap.add_argument("--dense-only", type=int, default=0,
+                    help="time N tensor-core Gram products X^H X and N block updates X M on the workload's "
+                         "n x p block instead of solves")
     ap.add_argument("--kernel", type=int, default=0,
                     help="filter-only: pin the step kernel (0 autotune, 1 SELL, 2 SELL two-step, 3 CSR)")
     ap.add_argument("--requests", type=int, default=24, help="serving workload: number of requests")
@@ -271,6 +274,8 @@ def ours_arm(args, dist):
 
     if args.filter_only:
         return filter_only(args, dist, B, ctx, M, A, w, peak, peak_kind)
+    if args.dense_only:
+        return dense_only(args, dist, B, ctx, A, w, stream)
 
     for _ in range(args.warmup):
         one_solve()
@@ -704,6 +709,61 @@ def filter_only(args, dist, B, ctx, M, A, w, peak, peak_kind):
     if dist.rank == 0:
         print(json.dumps({"mode": "filter-only", "workload": args.workload, "degree": args.degree,
                           "applications": args.filter_only, "seconds": dt}), flush=True)
+
+
+def dense_only(args, dist, B, ctx, A, w, stream):
+    """Time the dense products of one outer iteration on the tensor cores:
+    G = X^H X (apf_gram_tc) and Z = X M (apf_block_update) on the workload's
+    n x p block, with CUDA events on the library's stream.  The tensor-pipe
+    rate counts the bf16 MMAs the digit scheme issues: 28 digit pairs x
+    2 x 128 x 32 x 32 flops per 32-row chunk of each 128 x 32 output tile."""
+    import math
+    import numpy as np
+    import torch
+    from synth import rng
+    n, p, cplx = A.n, w.p, A.is_complex
+    C = 2 if cplx else 1
+    X = torch.from_numpy(rng.uniform_block(w.seed, rng.STREAM_INIT_BLOCK, n, p, cplx)).cuda()
+    Mt = torch.from_numpy(rng.uniform_block(w.seed, rng.STREAM_TEST, p, p, cplx)).cuda()
+    G = torch.empty((p, p), dtype=X.dtype, device="cuda")
+    Z = torch.empty_like(X)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(max(1, args.warmup)):
+        B.gram_tc(ctx, X, X, G)
+        B.block_update(ctx, X, Mt, Z)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.dense_only):
+        B.gram_tc(ctx, X, X, G)
+    ev[1].record(stream)
+    for _ in range(args.dense_only):
+        B.block_update(ctx, X, Mt, Z)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    gram_ms = ev[0].elapsed_time(ev[1]) / args.dense_only
+    upd_ms = ev[1].elapsed_time(ev[2]) / args.dense_only
+    chunk_flops = 28 * 2 * 2 * 128 * 32 * 32
+    pP, nP = 128 * math.ceil(p / 128), 32 * math.ceil(p / 32)
+    gram_tiles = (pP // 128) * (C * nP // 32)
+    gram_mma = gram_tiles * (C * 32 * math.ceil(n / 32) // 32) * chunk_flops
+    upd_tiles = math.ceil(n / 128) * math.ceil(C * p / 32)
+    upd_mma = upd_tiles * math.ceil(C * p / 32) * chunk_flops
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        bf16 = 1900.0
+    fp64_flops = (8 if cplx else 2) * n * p * p
+    if dist.rank == 0:
+        print(json.dumps({
+            "mode": "dense-only", "workload": args.workload, "n": n, "p": p, "dtype": "c128" if cplx else "f64",
+            "gram_ms": gram_ms, "gram_tensor_tflops": gram_mma / gram_ms / 1e9,
+            "gram_tensor_frac_of_bf16_peak": gram_mma / gram_ms / 1e9 / bf16,
+            "gram_fp64_equivalent_tflops": fp64_flops / gram_ms / 1e9,
+            "update_ms": upd_ms, "update_tensor_tflops": upd_mma / upd_ms / 1e9,
+            "update_tensor_frac_of_bf16_peak": upd_mma / upd_ms / 1e9 / bf16,
+            "update_fp64_equivalent_tflops": fp64_flops / upd_ms / 1e9,
+            "bf16_peak_tflops": bf16, "calls": args.dense_only}), flush=True)
 
 
 def main():

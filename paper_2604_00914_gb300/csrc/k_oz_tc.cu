@@ -16,23 +16,26 @@
 // dropping the pairs s + t >= 7 (below 2^-56 of the leading term, as the
 // rounding of F).  P_d over a chunk of 32 values of k is an integer below
 // 7 x 32 x 2^14 < 2^22, so the tensor cores' FP32 accumulation is exact in
-// any order; after each chunk the seven sums are converted to integers and
-// carried exactly in two 64-bit integers,
-//     hi += P_0 2^16 + P_1 2^8 + P_2,   lo += P_3 2^24 + P_4 2^16 + P_5 2^8 + P_6,
-// so C = 2^(E_m + F_n - 62) (hi 2^32 + lo) is formed once, in FP64, at the end.
-// (FP64 arithmetic runs at a tiny fraction of the tensor rate on this part:
-// the carry never touches it.)  Split-K partial sums are added with 64-bit
+// any order.  After each chunk the seven FP32 sums are turned into integers
+// exactly by adding 1.5 x 2^23 (the integer then sits in the low mantissa
+// bits) and accumulated in 32-bit integers (at most 512 chunks per CTA keeps
+// them below 2^31); at the end of the CTA they are folded into two 64-bit
+// integers,  hi = P_0 2^16 + P_1 2^8 + P_2,  lo = P_3 2^24 + P_4 2^16 + P_5 2^8 + P_6,
+// so C = 2^(E_m + F_n - 62) (hi 2^32 + lo) is formed once, in FP64.  (FP64
+// arithmetic runs at a tiny fraction of the tensor rate on this part: the
+// carry never touches it.)  Split-K partial sums are added with 64-bit
 // integer atomics, which is exact and independent of the order.
 //
-// Kernel (one CTA per 128 x 32 output tile and K range, 192 threads):
-//   warp 4  TMA producer: per 32-wide k chunk, one 3-D tensor copy of the
+// Kernel (one CTA per 128 x 32 output tile and K range, 320 threads):
+//   warp 8  TMA producer: per 32-wide k chunk, one 3-D tensor copy of the
 //           seven 128 x 32 slices of A and one of the seven 32 x 32 slices
 //           of B (64-byte swizzle) into a two-stage ring;
-//   warp 5  MMA issuer: 28 slice pairs x 2 k steps of tcgen05.mma
+//   warp 9  MMA issuer: 28 slice pairs x 2 k steps of tcgen05.mma
 //           (M = 128, N = 32, K = 16, bf16 in, FP32 accumulate) into one of
 //           two sets of seven TMEM accumulators (7 x 32 columns each);
-//   warps 0-3  drain: read the accumulators with tcgen05.ld (warp w owns TMEM
-//           lanes 32w..32w+31, i.e. rows of the tile), convert and carry.
+//   warps 0-7  drain: read the accumulators with tcgen05.ld (warp w owns TMEM
+//           lanes 32 (w mod 4) .. +31, i.e. rows of the tile, and columns
+//           16 (w / 4) .. +15) and accumulate the integers.
 // The stages and accumulator sets are handed over with mbarriers; every wait
 // is bounded in time and a timeout makes all roles stop, let their copies
 // land, free the TMEM and record DEV_BARRIER_TIMEOUT.
@@ -89,6 +92,12 @@ __device__ __forceinline__ void oz_digits(double x, int E, int (&dg)[OZS]) {
     F = (F - d) >> 8;
   }
   dg[0] = (int)F;
+}
+
+// v 2^e for |e| <= 2044 by two exact power-of-two multiplies (no library call)
+__device__ __forceinline__ double oz_scale(double v, int e) {
+  const int e1 = e / 2, e2 = e - e1;
+  return v * __longlong_as_double((long long)(1023 + e1) << 52) * __longlong_as_double((long long)(1023 + e2) << 52);
 }
 
 __device__ __forceinline__ __nv_bfloat16 oz_bf16(int v) { return __float2bfloat16_rn((float)v); }
@@ -286,6 +295,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "r"(taddr)
                : "memory");
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // shared-memory matrix descriptor: K-major, 64-byte swizzle (8-row atoms of
@@ -346,7 +364,11 @@ struct OzArgs {
   uint64_t limit_ns;
 };
 
-__global__ void __launch_bounds__(192, 1)
+constexpr int OZ_THREADS = 320;
+constexpr int OZ_DRAIN = 256;       // drain threads (warps 0-7)
+constexpr int OZ_MAX_CHUNKS = 512;  // per CTA: keeps the 32-bit sums below 2^31
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
 k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1 KB-aligned operand area (the swizzle atoms need 512-byte alignment)
@@ -373,7 +395,7 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       mbar_init(full + i, 1);
       mbar_init(empty + i, 1);
       mbar_init(tfull + i, 1);
-      mbar_init(tempty + i, 128);
+      mbar_init(tempty + i, OZ_DRAIN);
     }
     *abort_flag = 0;
     fence_mbar_init();
@@ -390,7 +412,7 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   // the imaginary half of a complex Gram: B rows from the other half of k, negated in the second
   const bool im_tile = a.mode == 0 && n0 >= a.n_im0;
 
-  if (warp == 4) {
+  if (warp == 8) {
     if (lane == 0) {
       for (int c = 0; c < nch; ++c) {
         const int st = c & 1;
@@ -403,7 +425,7 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         tma_load_3d(opB + st * OZ_B_STAGE, &tmB, (int)(kb * OZ_KC), im_tile ? n0 - a.n_im0 : n0, 0, full + st);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     if (lane == 0) {
       const uint32_t id_pos = umma_idesc(OZ_BM, OZ_BN, false);
       const uint32_t id_neg = umma_idesc(OZ_BM, OZ_BN, true);
@@ -433,11 +455,18 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       }
     }
   } else {
-    // drain: thread = row 32 warp + lane of the tile
-    long long hi[OZ_BN], lo[OZ_BN];
+    // drain: thread = row 32 (warp mod 4) + lane of the tile, columns 16 (warp / 4) + 0..15
+    constexpr int HC = OZ_BN / 2;
+    const int quarter = warp & 3, half = warp >> 2;
+    int acc[OZS][HC];
 #pragma unroll
-    for (int j = 0; j < OZ_BN; ++j) hi[j] = lo[j] = 0;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    for (int d = 0; d < OZS; ++d)
+#pragma unroll
+      for (int j = 0; j < HC; ++j) acc[d][j] = 0;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    // an exact FP32 integer v, |v| < 2^22: the bits of v + 1.5 2^23 are MAGIC + v
+    constexpr float kMagicF = 12582912.0f;
+    constexpr int kMagicI = 0x4B400000;
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
       const int b = c & 1;
@@ -446,41 +475,54 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         break;
       }
       tc_fence_after();
+      // one diagonal (16 columns) per load: the 112 sums stay in registers
 #pragma unroll
-      for (int g = 0; g < OZ_BN / 8; ++g) {
-        uint32_t r[OZS][8];
-#pragma unroll
-        for (int d = 0; d < OZS; ++d) tmem_ld8(tbase + lane_off + (uint32_t)(b * OZ_ACC + d * OZ_BN + g * 8), r[d]);
+      for (int d = 0; d < OZS; ++d) {
+        uint32_t r[HC];
+        tmem_ld16(tbase + lane_off + (uint32_t)(b * OZ_ACC + d * OZ_BN + half * HC), r);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          long long P[OZS];
-#pragma unroll
-          for (int d = 0; d < OZS; ++d) P[d] = (long long)__float2int_rn(__uint_as_float(r[d][j]));
-          hi[g * 8 + j] += (P[0] << 16) + (P[1] << 8) + P[2];
-          lo[g * 8 + j] += (P[3] << 24) + (P[4] << 16) + (P[5] << 8) + P[6];
-        }
+        for (int j = 0; j < HC; ++j)
+          acc[d][j] += __float_as_int(__fadd_rn(__uint_as_float(r[j]), kMagicF)) - kMagicI;
       }
       tc_fence_before();
       mbar_arrive(tempty + b);
     }
     if (ok && !*abort_flag) {
-      const int m = m0 + warp * 32 + lane;
-      if (a.mode == 0) {
+      // park the sums in the (now idle) operand area: the fold below then
+      // needs few registers.  The last tfull wait means every MMA, hence every
+      // read of the operand area and every TMA write into it, has completed.
+      int* sacc = reinterpret_cast<int*>(opA) + threadIdx.x * (OZS * HC + 1);
 #pragma unroll
-        for (int j = 0; j < OZ_BN; ++j) {
-          const int64_t o = (int64_t)m * a.NP + n0 + j;
-          if (hi[j]) atomicAdd(a.H + o, (unsigned long long)hi[j]);
-          if (lo[j]) atomicAdd(a.L + o, (unsigned long long)lo[j]);
+      for (int d = 0; d < OZS; ++d)
+#pragma unroll
+        for (int j = 0; j < HC; ++j) sacc[d * HC + j] = acc[d][j];
+      const int m = m0 + quarter * 32 + lane;
+      const int nb0 = n0 + half * HC;
+      auto fold = [&](int j, long long& hi, long long& lo) {
+        hi = ((long long)sacc[0 * HC + j] << 16) + ((long long)sacc[1 * HC + j] << 8) + sacc[2 * HC + j];
+        lo = ((long long)sacc[3 * HC + j] << 24) + ((long long)sacc[4 * HC + j] << 16) +
+             ((long long)sacc[5 * HC + j] << 8) + sacc[6 * HC + j];
+      };
+      if (a.mode == 0) {
+#pragma unroll 1
+        for (int j = 0; j < HC; ++j) {
+          long long hi, lo;
+          fold(j, hi, lo);
+          const int64_t o = (int64_t)m * a.NP + nb0 + j;
+          if (hi) atomicAdd(a.H + o, (unsigned long long)hi);
+          if (lo) atomicAdd(a.L + o, (unsigned long long)lo);
         }
       } else if (m < a.nrows) {
         const int em = a.ea[m];
-#pragma unroll
-        for (int j = 0; j < OZ_BN; ++j) {
-          const int col = n0 + j;
+#pragma unroll 1
+        for (int j = 0; j < HC; ++j) {
+          const int col = nb0 + j;
           if (col >= a.ncols) continue;
+          long long hi, lo;
+          fold(j, hi, lo);
           const int sc = em + a.fb[col] - 62;
-          const double v = ldexp((double)hi[j], sc + 32) + ldexp((double)lo[j], sc);
+          const double v = oz_scale((double)hi, sc + 32) + oz_scale((double)lo, sc);
           int64_t oz, oz0;
           if (a.cplx) {
             const int jc = col % a.pb, part = col / a.pb;
@@ -530,7 +572,7 @@ __global__ void k_oz_gram_finish(int pa, int pb, int NP, int n_im0, bool hermiti
   auto val = [&](int col) {
     const int64_t o = (int64_t)si * NP + col;
     const int sc = ea[si] + eb[sj] - 62;
-    return ldexp((double)(long long)H[o], sc + 32) + ldexp((double)(long long)L[o], sc);
+    return oz_scale((double)(long long)H[o], sc + 32) + oz_scale((double)(long long)L[o], sc);
   };
   const double re = val(sj);
   if constexpr (ScalarTraits<T>::is_complex) {
@@ -569,7 +611,8 @@ static void launch_oz(apf_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb
   allow_large_smem_bytes<k_oz_umma>(ctx->device, (int)OZ_SMEM);
   a.err = ctx->d_err;
   a.limit_ns = filter_wait_ns(ctx);
-  k_oz_umma<<<dim3((unsigned)ntiles, (unsigned)nsplit), 192, OZ_SMEM, ctx->stream>>>(ma, mb, a);
+  APF_REQUIRE(a.chunks_per_split <= OZ_MAX_CHUNKS, APF_ERR_ARG);
+  k_oz_umma<<<dim3((unsigned)ntiles, (unsigned)nsplit), OZ_THREADS, OZ_SMEM, ctx->stream>>>(ma, mb, a);
   count_launch(ctx);
 }
 
@@ -581,7 +624,7 @@ void gram_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_
   APF_REQUIRE(n >= 1 && pa <= APF_MAX_P && pb <= APF_MAX_P, APF_ERR_ARG);
   constexpr int C = ScalarTraits<T>::is_complex ? 2 : 1;
   const int64_t nK = round_up(n, OZ_KC), KT = C * nK;
-  // exactness of the carry: at most 2^16 chunks of k
+  // exactness of the carry: at most 2^16 chunks of k in all
   if (KT / OZ_KC > 65536) { gram<T>(ctx, n, pa, pb, X, ldx, Y, ldy, G, ldg, hermitian); return; }
   const int paP = (int)round_up(pa, OZ_BM), pbP = (int)round_up(pb, OZ_BN);
   const int NP = C * pbP;  // output columns: [re | im]
@@ -644,6 +687,7 @@ void gram_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_
   const int ntiles = (int)tiles.size();
   int64_t nsplit = (2LL * ctx->num_sms + ntiles - 1) / ntiles;
   nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, a.chunks / 8 > 0 ? a.chunks / 8 : 1));
+  nsplit = std::max<int64_t>(nsplit, (a.chunks + OZ_MAX_CHUNKS - 1) / OZ_MAX_CHUNKS);
   a.chunks_per_split = (a.chunks + nsplit - 1) / nsplit;
   nsplit = (a.chunks + a.chunks_per_split - 1) / a.chunks_per_split;
   launch_oz(ctx, ma, mb, a, ntiles, (int)nsplit);
