@@ -27,9 +27,10 @@
 // integer atomics, which is exact and independent of the order.
 //
 // Kernel (one CTA per 128 x 32 output tile and K range, 320 threads):
-//   warp 8  TMA producer: per 32-wide k chunk, one 3-D tensor copy of the
-//           seven 128 x 32 slices of A and one of the seven 32 x 32 slices
-//           of B (64-byte swizzle) into a two-stage ring;
+//   warp 8  producer: per 32-wide k chunk, bulk copies (cp.async.bulk) of the
+//           seven 128 x 32 digit tiles of A and the seven 32 x 32 tiles of B,
+//           stored pre-swizzled (64-byte swizzle) in global memory, into a
+//           three-stage ring;
 //   warp 9  MMA issuer: 28 slice pairs x 2 k steps of tcgen05.mma
 //           (M = 128, N = 32, K = 16, bf16 in, FP32 accumulate) into one of
 //           two sets of seven TMEM accumulators (7 x 32 columns each);
@@ -44,7 +45,6 @@
 
 #include "apf_internal.h"
 #include "spmm_sell.cuh"
-#include "tma.h"
 
 namespace apf {
 
@@ -57,7 +57,17 @@ constexpr uint32_t OZ_A_SLICE = OZ_BM * OZ_KC * 2;   // 8 KB
 constexpr uint32_t OZ_B_SLICE = OZ_BN * OZ_KC * 2;   // 2 KB
 constexpr uint32_t OZ_A_STAGE = OZS * OZ_A_SLICE;    // 56 KB
 constexpr uint32_t OZ_B_STAGE = OZS * OZ_B_SLICE;    // 14 KB
-constexpr size_t OZ_SMEM = 1024 + 2 * (size_t)(OZ_A_STAGE + OZ_B_STAGE) + 1024;
+constexpr int OZ_STAGES = 3;                        // operand ring depth
+constexpr size_t OZ_SMEM = 1024 + OZ_STAGES * (size_t)(OZ_A_STAGE + OZ_B_STAGE) + 1024;
+
+// Digit layout in global memory: chunk-major planes S[kc][s][row][32 k], each
+// 64-byte row already in the 64-byte-swizzled order the MMA reads from shared
+// memory (16-byte unit u of row r stored at u ^ ((r >> 1) & 3)), so one
+// contiguous bulk copy brings a slice's 128-row (or 32-row) tile of a chunk
+// into its shared-memory image.
+__device__ __forceinline__ int64_t oz_off(int64_t kc, int s, int64_t row, int64_t rowsP, int kk) {
+  return ((kc * OZS + s) * rowsP + row) * OZ_KC + ((((kk >> 3) ^ (int)((row >> 1) & 3)) << 3) | (kk & 7));
+}
 
 // ---- digits ----------------------------------------------------------------
 __device__ __forceinline__ double oz_abs_max(double v) { return fabs(v); }
@@ -163,7 +173,10 @@ k_ozt_split_cols(int64_t n, int p, const T* __restrict__ X, int64_t ld, const in
 #pragma unroll
     for (int s = 0; s < OZS; ++s)
 #pragma unroll
-      for (int c = 0; c < C; ++c) S[((int64_t)s * pP + a) * KT + (int64_t)c * nK + i] = tile[s][c][r][tx];
+      for (int c = 0; c < C; ++c) {
+        const int64_t k = (int64_t)c * nK + i;
+        S[oz_off(k / OZ_KC, s, a, pP, (int)(k % OZ_KC))] = tile[s][c][r][tx];
+      }
   }
 }
 
@@ -201,7 +214,7 @@ k_ozt_split_rows(int64_t n, int p, const T* __restrict__ X, int64_t ld, const in
   int dg[OZS];
   oz_digits(x, e[i], dg);
 #pragma unroll
-  for (int s = 0; s < OZS; ++s) S[((int64_t)s * nP + i) * KT + k] = oz_bf16(dg[s]);
+  for (int s = 0; s < OZS; ++s) S[oz_off(k / OZ_KC, s, i, nP, k % OZ_KC)] = oz_bf16(dg[s]);
 }
 
 // The real form of a small factor M (pa x pb, ldm): Bt[j][k] = Mt[k][j] with
@@ -246,18 +259,11 @@ k_ozt_split_small(int pa, int pb, const T* __restrict__ M, int64_t ldm, int NP, 
     int dg[OZS];
     oz_digits(value(k), E, dg);
 #pragma unroll
-    for (int s = 0; s < OZS; ++s) S[((int64_t)s * NP + j) * KT + k] = oz_bf16(dg[s]);
+    for (int s = 0; s < OZS; ++s) S[oz_off(k / OZ_KC, s, j, NP, (int)(k % OZ_KC))] = oz_bf16(dg[s]);
   }
 }
 
 // ---- tcgen05 primitives ---------------------------------------------------------
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
-      : "memory");
-}
 __device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
                    smem_addr(bar)),
@@ -338,6 +344,9 @@ __device__ __forceinline__ bool oz_wait(uint64_t* bar, uint32_t parity, uint64_t
 }
 
 struct OzArgs {
+  const __nv_bfloat16* SA;  // digit planes of A (rowsA rows) and B (rowsB rows)
+  const __nv_bfloat16* SB;
+  int64_t rowsA, rowsB;
   int mode;          // 0: Gram (int64 atomics into H, L); 1: tall product (FP64 out)
   int64_t chunks;    // k chunks of this product (KT / OZ_KC)
   int64_t chunks_per_split;
@@ -369,19 +378,19 @@ constexpr int OZ_DRAIN = 256;       // drain threads (warps 0-7)
 constexpr int OZ_MAX_CHUNKS = 512;  // per CTA: keeps the 32-bit sums below 2^31
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs a) {
+k_oz_umma(OzArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1 KB-aligned operand area (the swizzle atoms need 512-byte alignment)
   const uint32_t base_s = smem_addr(smem_raw);
   unsigned char* smem = smem_raw + ((1024 - (base_s & 1023)) & 1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem);        // [2] TMA -> MMA
-  uint64_t* empty = full + 2;                                 // [2] MMA -> TMA
-  uint64_t* tfull = full + 4;                                 // [2] MMA -> drain
-  uint64_t* tempty = full + 6;                                // [2] drain -> MMA
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(full + 8);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(full + 9);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);        // [3] bulk copies -> MMA
+  uint64_t* empty = full + OZ_STAGES;                         // [3] MMA -> producer
+  uint64_t* tfull = empty + OZ_STAGES;                        // [2] MMA -> drain
+  uint64_t* tempty = tfull + 2;                               // [2] drain -> MMA
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tempty + 3);
   unsigned char* opA = smem + 1024;
-  unsigned char* opB = opA + 2 * OZ_A_STAGE;
+  unsigned char* opB = opA + OZ_STAGES * OZ_A_STAGE;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int2 tile = a.tiles[blockIdx.x];
@@ -391,9 +400,11 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   const int nch = (int)(c_end > c_begin ? c_end - c_begin : 0);
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < OZ_STAGES; ++i) {
       mbar_init(full + i, 1);
       mbar_init(empty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(tfull + i, 1);
       mbar_init(tempty + i, OZ_DRAIN);
     }
@@ -414,15 +425,18 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
   if (warp == 8) {
     if (lane == 0) {
+      const int nb = im_tile ? n0 - a.n_im0 : n0;
       for (int c = 0; c < nch; ++c) {
-        const int st = c & 1;
-        if (c >= 2 && !oz_wait(empty + st, (uint32_t)(((c >> 1) - 1) & 1), a.limit_ns, abort_flag)) break;
+        const int st = c % OZ_STAGES, use = c / OZ_STAGES;
+        if (c >= OZ_STAGES && !oz_wait(empty + st, (uint32_t)((use - 1) & 1), a.limit_ns, abort_flag)) break;
         const int64_t kc = c_begin + c;
         int64_t kb = kc;
         if (im_tile) kb = kc < a.half_chunks ? kc + a.half_chunks : kc - a.half_chunks;
         mbar_arrive_expect(full + st, OZ_A_STAGE + OZ_B_STAGE);
-        tma_load_3d(opA + st * OZ_A_STAGE, &tmA, (int)(kc * OZ_KC), m0, 0, full + st);
-        tma_load_3d(opB + st * OZ_B_STAGE, &tmB, (int)(kb * OZ_KC), im_tile ? n0 - a.n_im0 : n0, 0, full + st);
+        for (int sl = 0; sl < OZS; ++sl) {
+          bulk_g2s(opA + st * OZ_A_STAGE + sl * OZ_A_SLICE, a.SA + oz_off(kc, sl, m0, a.rowsA, 0), OZ_A_SLICE, full + st);
+          bulk_g2s(opB + st * OZ_B_STAGE + sl * OZ_B_SLICE, a.SB + oz_off(kb, sl, nb, a.rowsB, 0), OZ_B_SLICE, full + st);
+        }
       }
     }
   } else if (warp == 9) {
@@ -430,8 +444,8 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const uint32_t id_pos = umma_idesc(OZ_BM, OZ_BN, false);
       const uint32_t id_neg = umma_idesc(OZ_BM, OZ_BN, true);
       for (int c = 0; c < nch; ++c) {
-        const int st = c & 1, b = c & 1;
-        if (!oz_wait(full + st, (uint32_t)((c >> 1) & 1), a.limit_ns, abort_flag)) break;
+        const int st = c % OZ_STAGES, b = c & 1;
+        if (!oz_wait(full + st, (uint32_t)((c / OZ_STAGES) & 1), a.limit_ns, abort_flag)) break;
         if (c >= 2 && !oz_wait(tempty + b, (uint32_t)(((c >> 1) - 1) & 1), a.limit_ns, abort_flag)) break;
         tc_fence_after();
         const uint32_t idesc = (im_tile && c_begin + c >= a.half_chunks) ? id_neg : id_pos;
@@ -546,10 +560,10 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     // their barriers (bounded) before the shared memory and TMEM go away
     if (threadIdx.x == 0) {
       volatile int dummy = 0;
-      for (int c = (nch > 2 ? nch - 2 : 0); c < nch; ++c) {
-        oz_wait(full + (c & 1), (uint32_t)((c >> 1) & 1), 1000000000ull, &dummy);
+      for (int c = (nch > OZ_STAGES ? nch - OZ_STAGES : 0); c < nch; ++c)
+        oz_wait(full + c % OZ_STAGES, (uint32_t)((c / OZ_STAGES) & 1), 1000000000ull, &dummy);
+      for (int c = (nch > 2 ? nch - 2 : 0); c < nch; ++c)
         oz_wait(tfull + (c & 1), (uint32_t)((c >> 1) & 1), 1000000000ull, &dummy);
-      }
     }
     __syncthreads();
   }
@@ -597,22 +611,12 @@ static void* workspace(apf_ctx* ctx, size_t bytes) {
   return ctx->ws;
 }
 
-static bool tmap_slices(CUtensorMap* out, const __nv_bfloat16* S, int64_t KT, int64_t rows, int box_rows) {
-  // 3-D map (k, row, slice) over S[s][row][k]
-  const cuuint64_t dims[3] = {(cuuint64_t)KT, (cuuint64_t)rows, (cuuint64_t)OZS};
-  const cuuint64_t strides[2] = {(cuuint64_t)KT * 2, (cuuint64_t)rows * KT * 2};
-  const cuuint32_t box[3] = {(cuuint32_t)OZ_KC, (cuuint32_t)box_rows, (cuuint32_t)OZS};
-  return encode_tmap(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S, dims, strides, box,
-                     CU_TENSOR_MAP_SWIZZLE_64B);
-}
-
-static void launch_oz(apf_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, OzArgs& a, int ntiles,
-                      int nsplit) {
+static void launch_oz(apf_ctx* ctx, OzArgs& a, int ntiles, int nsplit) {
   allow_large_smem_bytes<k_oz_umma>(ctx->device, (int)OZ_SMEM);
   a.err = ctx->d_err;
   a.limit_ns = filter_wait_ns(ctx);
   APF_REQUIRE(a.chunks_per_split <= OZ_MAX_CHUNKS, APF_ERR_ARG);
-  k_oz_umma<<<dim3((unsigned)ntiles, (unsigned)nsplit), OZ_THREADS, OZ_SMEM, ctx->stream>>>(ma, mb, a);
+  k_oz_umma<<<dim3((unsigned)ntiles, (unsigned)nsplit), OZ_THREADS, OZ_SMEM, ctx->stream>>>(a);
   count_launch(ctx);
 }
 
@@ -672,10 +676,11 @@ void gram_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_
   slice(X, ldx, pa, paP, ex, SX);
   if (!same) slice(Y, ldy, pb, pyP, ey, SY);
 
-  CUtensorMap ma, mb;
-  APF_REQUIRE(tmap_slices(&ma, SX, KT, paP, OZ_BM), APF_ERR_CUDA);
-  APF_REQUIRE(tmap_slices(&mb, SY, KT, pyP, OZ_BN), APF_ERR_CUDA);
   OzArgs a{};
+  a.SA = SX;
+  a.SB = SY;
+  a.rowsA = paP;
+  a.rowsB = pyP;
   a.mode = 0;
   a.chunks = KT / OZ_KC;
   a.half_chunks = nK / OZ_KC;
@@ -690,7 +695,7 @@ void gram_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_
   nsplit = std::max<int64_t>(nsplit, (a.chunks + OZ_MAX_CHUNKS - 1) / OZ_MAX_CHUNKS);
   a.chunks_per_split = (a.chunks + nsplit - 1) / nsplit;
   nsplit = (a.chunks + a.chunks_per_split - 1) / a.chunks_per_split;
-  launch_oz(ctx, ma, mb, a, ntiles, (int)nsplit);
+  launch_oz(ctx, a, ntiles, (int)nsplit);
   k_oz_gram_finish<T><<<(unsigned)((pa * pb + 255) / 256), 256, 0, ctx->stream>>>(
       (int)pa, (int)pb, NP, C == 2 ? pbP : 0, hermitian, H, L, ex, ey, G, ldg);
   count_launch(ctx);
@@ -730,10 +735,11 @@ void gemm_tall_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, i
                                                                                      SA);
   k_ozt_split_small<T, C><<<(unsigned)NT, 256, 0, ctx->stream>>>((int)pa, (int)pb, M, ldm, NT, KT, SB, fb);
   count_launch(ctx, 3);
-  CUtensorMap ma, mb;
-  APF_REQUIRE(tmap_slices(&ma, SA, KT, nP, OZ_BM), APF_ERR_CUDA);
-  APF_REQUIRE(tmap_slices(&mb, SB, KT, NT, OZ_BN), APF_ERR_CUDA);
   OzArgs a{};
+  a.SA = SA;
+  a.SB = SB;
+  a.rowsA = nP;
+  a.rowsB = NT;
   a.mode = 1;
   a.chunks = KT / OZ_KC;
   a.chunks_per_split = a.chunks;
@@ -751,7 +757,7 @@ void gemm_tall_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, i
   a.ldz0 = Z0 ? ldz0 : ldz;
   a.alpha = alpha;
   a.beta = Z0 ? beta : 0.0;
-  launch_oz(ctx, ma, mb, a, ntm * ntn, 1);
+  launch_oz(ctx, a, ntm * ntn, 1);
 }
 template void gemm_tall_tc<double>(apf_ctx*, int64_t, int64_t, int64_t, const double*, int64_t, const double*,
                                    int64_t, double*, int64_t, double, double, const double*, int64_t);
