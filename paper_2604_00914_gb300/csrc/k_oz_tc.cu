@@ -283,12 +283,19 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
+// D = A B^T (the first product of an accumulation) and D += A B^T
+__device__ __forceinline__ void umma_bf16_first(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, 0, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_bf16_acc(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.eq.b32 p, 0, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -449,18 +456,21 @@ k_oz_umma(OzArgs a) {
         if (c >= 2 && !oz_wait(tempty + b, (uint32_t)(((c >> 1) - 1) & 1), a.limit_ns, abort_flag)) break;
         tc_fence_after();
         const uint32_t idesc = (im_tile && c_begin + c >= a.half_chunks) ? id_neg : id_pos;
-        const uint32_t sa = smem_addr(opA + st * OZ_A_STAGE), sb = smem_addr(opB + st * OZ_B_STAGE);
-#pragma unroll 1
+        // descriptors of the stage's first tiles; the other tiles are at fixed
+        // offsets (the 14-bit address field holds addr / 16 and never carries)
+        const uint64_t ad0 = umma_desc_sw64(smem_addr(opA + st * OZ_A_STAGE));
+        const uint64_t bd0 = umma_desc_sw64(smem_addr(opB + st * OZ_B_STAGE));
+        const uint32_t dt0 = tbase + (uint32_t)(b * OZ_ACC);
+#pragma unroll
         for (int d = 0; d < OZS; ++d) {
-          const uint32_t dt = tbase + (uint32_t)(b * OZ_ACC + d * OZ_BN);
-#pragma unroll 1
+#pragma unroll
           for (int s = 0; s <= d; ++s) {
-            const int t = d - s;
 #pragma unroll
             for (int kk = 0; kk < OZ_KC / 16; ++kk) {
-              const uint64_t ad = umma_desc_sw64(sa + s * OZ_A_SLICE + kk * 32);
-              const uint64_t bd = umma_desc_sw64(sb + t * OZ_B_SLICE + kk * 32);
-              umma_bf16(dt, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+              const uint64_t ad = ad0 + (uint64_t)((s * OZ_A_SLICE + kk * 32) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)(((d - s) * OZ_B_SLICE + kk * 32) >> 4);
+              if (s == 0 && kk == 0) umma_bf16_first(dt0 + d * OZ_BN, ad, bd, idesc);
+              else umma_bf16_acc(dt0 + d * OZ_BN, ad, bd, idesc);
             }
           }
         }
@@ -489,15 +499,20 @@ k_oz_umma(OzArgs a) {
         break;
       }
       tc_fence_after();
-      // one diagonal (16 columns) per load: the 112 sums stay in registers
+      // two diagonals (16 columns each) per wait: the 112 sums stay in registers
 #pragma unroll
-      for (int d = 0; d < OZS; ++d) {
-        uint32_t r[HC];
-        tmem_ld16(tbase + lane_off + (uint32_t)(b * OZ_ACC + d * OZ_BN + half * HC), r);
+      for (int d0 = 0; d0 < OZS; d0 += 2) {
+        uint32_t r0[HC], r1[HC];
+        tmem_ld16(tbase + lane_off + (uint32_t)(b * OZ_ACC + d0 * OZ_BN + half * HC), r0);
+        if (d0 + 1 < OZS) tmem_ld16(tbase + lane_off + (uint32_t)(b * OZ_ACC + (d0 + 1) * OZ_BN + half * HC), r1);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < HC; ++j)
-          acc[d][j] += __float_as_int(__fadd_rn(__uint_as_float(r[j]), kMagicF)) - kMagicI;
+          acc[d0][j] += __float_as_int(__fadd_rn(__uint_as_float(r0[j]), kMagicF)) - kMagicI;
+        if (d0 + 1 < OZS)
+#pragma unroll
+          for (int j = 0; j < HC; ++j)
+            acc[d0 + 1][j] += __float_as_int(__fadd_rn(__uint_as_float(r1[j]), kMagicF)) - kMagicI;
       }
       tc_fence_before();
       mbar_arrive(tempty + b);
