@@ -159,6 +159,27 @@ def anderson3d_r_48_slices() -> SliceWorkload:
 
 _BUILDERS["anderson3d_r_48_slices"] = lambda seed: matrices.anderson(48, 3, 6.0, seed, complex_phases=False)
 
+
+def anderson3d_r_80_slices() -> SliceWorkload:
+    """Batched spectrum slicing of one real 3D Anderson model, 80^3 periodic
+    (n = 512,000), on-site disorder U[-3, 3]: sixteen contiguous slices with
+    seeded uneven target counts in [20, 150] (56..141 here, 1,480 in all),
+    starting above the 200th eigenvalue, edges from the oracle's count
+    estimate (stored in tests/golden); block m = ceil(1.5 count) per slice
+    (2,232 columns in all)."""
+    import math
+    path = os.path.join(_GOLDEN, "slices_anderson3d_r_80.json")
+    with open(path) as f:
+        d = json.load(f)
+    b = [float(np.nextafter(x, -np.inf)) for x in d["b"]]
+    p = [int(math.ceil(1.5 * c)) for c in d["target_counts"]]
+    return SliceWorkload("anderson3d_r_80_slices", BASE_SEED + 3, list(d["a"]), b, p, False,
+                         "3D Anderson 80^3 periodic, W=6, real, 16 slices above the 200th eigenvalue, "
+                         "p = 1.5 count")
+
+
+_BUILDERS["anderson3d_r_80_slices"] = _c4_matrix
+
 WORKLOADS = {
     "lap2d_32": lap2d_32,
     "anderson3d_c_64": anderson3d_c_64,
@@ -169,6 +190,7 @@ WORKLOADS = {
 
 SLICE_WORKLOADS = {
     "anderson3d_r_48_slices": anderson3d_r_48_slices,
+    "anderson3d_r_80_slices": anderson3d_r_80_slices,
 }
 
 

@@ -20,7 +20,12 @@ Run from the repository root:  python tests/golden/make_golden.py
   filter of [lambda_min, E], bounds from the Gershgorin interval), so that the
   interval holds about 200 eigenvalues around the midpoint of the 300th-500th.
 
-    python tests/golden/make_golden.py [lap2d | slices48 | ks96]   (default: all)
+* slices_anderson3d_r_80.json -- sixteen contiguous slices of the real 80^3
+  Anderson model (W = 6) above its 200th eigenvalue with seeded uneven target
+  counts in [20, 150], edges from the oracle's count estimate (Chebyshev
+  moments of degree 3000 over 16 +-1 probes).
+
+    python tests/golden/make_golden.py [lap2d | slices48 | ks96 | slices80]   (default: all)
 """
 from __future__ import annotations
 
@@ -125,11 +130,59 @@ def ks8_96_interval(lo_count=300, hi_count=500, k=3000, probes=16):
     print("ks8_96:", a, b, "estimated count", out["count_estimate"])
 
 
+def slices_anderson80(nslices=16, start_count=200, k=3000, probes=16):
+    """Sixteen contiguous slices of the real 80^3 Anderson model (W = 6)
+    starting above its 200th eigenvalue (the low end of the band, where the
+    density of states is small), with seeded uneven target counts in
+    [20, 150]: slice s = [E_{N_s}, E_{N_{s+1}}] with N_0 = 200 and
+    N_{s+1} = N_s + count_s, E_N from the oracle's count estimate."""
+    seed = BASE_SEED + 3
+    A = matrices.anderson(80, 3, 6.0, seed, complex_phases=False).to_scipy()
+    lmin, lmax = fsi.gershgorin(A)
+    l1, l2 = cb.linear_map(lmin, lmax)
+    Z = rng.rademacher_block(seed, rng.STREAM_TEST, A.shape[0], probes)
+    mu = trace.chebyshev_trace_moments(A, l1, l2, Z, k)
+
+    def below(E):
+        coef = cb.filter_coefficients(-1.0, l1 * E + l2, k, cb.DAMP_LANCZOS_M, 0.5)
+        return float(coef @ mu)
+
+    def energy_at(count):
+        lo, hi = lmin, lmax
+        for _ in range(100):
+            mid = 0.5 * (lo + hi)
+            if below(mid) < count:
+                lo = mid
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+
+    u = rng.uniform(seed, rng.STREAM_TEST, np.arange(nslices, dtype=np.uint64))
+    counts = [20 + int(131 * x) for x in u]
+    cum = [start_count]
+    for c in counts:
+        cum.append(cum[-1] + c)
+    edges = [energy_at(c) for c in cum]
+    est = [below(edges[i + 1]) - below(edges[i]) for i in range(nslices)]
+    out = dict(a=edges[:-1], b=edges[1:], target_counts=counts, count_estimates=est, start_count=start_count,
+               gershgorin=[lmin, lmax], degree=k, probes=probes,
+               source=("oracle.trace.chebyshev_trace_moments (degree %d, %d probes of stream %d) on "
+                       "synth.matrices.anderson(80, 3, 6.0, %d, False); Gershgorin bounds; counts from "
+                       "synth.rng.uniform(%d, stream %d)" % (k, probes, rng.STREAM_TEST, seed, seed,
+                                                             rng.STREAM_TEST)))
+    with open(os.path.join(HERE, "slices_anderson3d_r_80.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print("anderson3d_r_80 slices: edges", [round(e, 4) for e in edges], "counts", counts,
+          "estimates", [round(c, 1) for c in est])
+
+
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["lap2d", "slices48", "ks96"]
+    which = sys.argv[1:] or ["lap2d", "slices48", "ks96", "slices80"]
     if "lap2d" in which:
         lap2d_interval()
     if "slices48" in which:
         slices_anderson48()
     if "ks96" in which:
         ks8_96_interval()
+    if "slices80" in which:
+        slices_anderson80()

@@ -67,3 +67,25 @@ def test_ks96_interval_agrees_with_the_weyl_count():
     assert abs(d["count_estimate"] - 200.0) < 1.0
     # the bound states of 64 wells of depth 1 sit below zero, a handful per well
     assert 20 <= d["count_below_zero"] <= 64 * 4
+
+
+def test_c4_slice_workload_shape():
+    """Sixteen disjoint contiguous slices, target counts in [20, 150], the
+    stored count estimates equal to the targets (the edges were placed by
+    them), m = ceil(1.5 count) per slice and more than 1024 columns in all."""
+    import json
+    import math
+    import os
+    w = workloads.anderson3d_r_80_slices()
+    assert len(w.a) == 16 and w.seed == workloads.BASE_SEED + 3
+    with open(os.path.join(os.path.dirname(__file__), "golden", "slices_anderson3d_r_80.json")) as f:
+        d = json.load(f)
+    assert all(20 <= c <= 150 for c in d["target_counts"])
+    assert np.allclose(d["count_estimates"], d["target_counts"], atol=0.5)
+    assert w.p == [math.ceil(1.5 * c) for c in d["target_counts"]] and sum(w.p) > 1024
+    for s in range(16):
+        assert w.a[s] < w.b[s]
+        if s:
+            assert w.b[s - 1] < w.a[s] and w.a[s] - w.b[s - 1] <= 1e-15
+    # the low end of the band: below the clean band edge -6, inside the Gershgorin range -9
+    assert -9.0 < w.a[0] and w.b[-1] < -6.0
