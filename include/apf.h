@@ -251,13 +251,20 @@ apf_status apf_result_history(const apf_result* r, double* host_out, int32_t cap
 apf_status apf_result_destroy(apf_result* r);
 
 /* ---- serving: many solves on one GPU -------------------------------------- */
-/* The paper solves one problem at a time; this loop runs independent
- * requests (Sec. 1: slices and problems need no communication) concurrently
- * on one device.  Requests are admitted in arrival order when their
+/* The paper solves one problem at a time; this loop serves independent
+ * requests (Sec. 1: slices and problems need no communication) with
+ * continuous batching on one device.  One engine thread advances every
+ * admitted request's Alg. 4 in lockstep outer iterations; requests are
+ * admitted in arrival order between iterations, when a slot is free and their
  * estimated device footprint fits in the budget left by the running ones (or
- * when none runs); each runs on its own context and CUDA stream, so the
- * running solves' kernels interleave.  A request's result does not depend on
- * what runs beside it. */
+ * when none runs).  In each iteration the Clenshaw steps (Alg. 2) of all
+ * running requests with an FP32 filter run together, one launch per step for
+ * all real and one for all complex problems (a request of lower degree joins
+ * the recurrence later; all finish on the same step); the dense steps then
+ * run concurrently, one CUDA stream per request.  Each request's subspace and
+ * filter state stays on the device from admission to completion.  A
+ * request's arithmetic does not depend on the other requests: its result is
+ * the same alone and in a mix, and the same as apf_solve's. */
 typedef struct apf_server apf_server;
 
 typedef struct {
@@ -270,13 +277,17 @@ typedef struct {
 } apf_request_info;
 
 typedef struct {
-  int32_t queued, running, peak_running, workers;
+  int32_t queued, running, peak_running, workers;  /* workers: most requests in flight at once */
   int64_t in_flight_bytes, peak_in_flight_bytes, budget_bytes, completed;
+  int64_t batched_launches;  /* Clenshaw-step launches that served the running requests together */
+  int32_t widest_batch;      /* most requests in one such launch */
+  int32_t reserved;
 } apf_server_info;
 
-/* Start `max_concurrent` (1..64) worker threads on `device`.  hbm_budget_bytes:
- * device bytes the running requests may reserve; 0 means 90 % of the memory
- * free at creation. */
+/* Start the serving engine on `device` with at most `max_concurrent` (1..64;
+ * more than 32 counts as 32) requests in flight.  hbm_budget_bytes: device
+ * bytes the running requests may reserve; 0 means 90 % of the memory free at
+ * creation. */
 apf_status apf_server_create(apf_server** out, int32_t device, int32_t max_concurrent,
                              int64_t hbm_budget_bytes);
 /* Queue one solve of the n x n Hermitian matrix (host CSR, both triangles,

@@ -92,7 +92,8 @@ class apf_server_info(C.Structure):
     _fields_ = [
         ("queued", C.c_int32), ("running", C.c_int32), ("peak_running", C.c_int32), ("workers", C.c_int32),
         ("in_flight_bytes", C.c_int64), ("peak_in_flight_bytes", C.c_int64), ("budget_bytes", C.c_int64),
-        ("completed", C.c_int64),
+        ("completed", C.c_int64), ("batched_launches", C.c_int64), ("widest_batch", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
     def as_dict(self):
@@ -422,7 +423,7 @@ class _RequestOwner:
 
 
 class Server:
-    """apf_server_*: concurrent solves of independent requests on one device."""
+    """apf_server_*: independent requests served with continuous batching on one device."""
 
     def __init__(self, device=0, max_concurrent=4, hbm_budget_bytes=0, lib=None):
         self.lib = lib or Library.load()

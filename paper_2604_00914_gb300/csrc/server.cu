@@ -1,13 +1,22 @@
-// Serving loop: many independent interior eigenproblems on one GPU.
+// Serving loop: many independent interior eigenproblems on one GPU, with
+// continuous batching.
 //
 // Requests (a Hermitian matrix in host CSR plus solver parameters) are queued
-// in arrival order.  A fixed pool of worker threads takes them off the queue;
-// the head of the queue is admitted when its estimated device footprint fits
-// in what the running solves leave of the HBM budget (or when nothing runs).
-// Each admitted request gets its own context, hence its own CUDA stream, so
-// the Clenshaw steps and dense steps of the running solves interleave on the
-// GPU.  The kernels' arithmetic does not depend on what else runs: a request
-// returns the same result alone and in a mix.
+// in arrival order.  One engine thread runs every admitted request's Alg. 4 in
+// lockstep outer iterations: the head of the queue is admitted between
+// iterations when a slot is free and its estimated device footprint fits in
+// what the running solves leave of the HBM budget (or when nothing runs), so a
+// request that arrives while others are on the GPU joins at their next
+// iteration.  In each iteration the Clenshaw steps (Alg. 2) of all running
+// requests go out together: step j of every request whose recurrence has
+// reached j runs in ONE launch (spmm_multi.cuh), real and complex problems in
+// one launch each; a request of lower degree joins the recurrence later and all
+// finish on the same step.  The orthogonalisation, Rayleigh-Ritz and residual
+// steps of the requests then run concurrently, each on its own CUDA stream.
+// Each request's state (subspace, locked vectors, filter buffers) stays on the
+// device from admission to completion.  The arithmetic of a request does not
+// depend on the other requests, so its result is the same alone and in a mix
+// (and the same as apf_solve's).
 //
 // The result of a request owns that request's context; apf_result_destroy
 // releases both.
@@ -21,6 +30,7 @@
 #include <thread>
 #include <vector>
 
+#include "engine.h"
 #include "solver.h"
 
 namespace {
@@ -61,8 +71,11 @@ struct apf_server {
   int32_t peak_running = 0;
   int64_t peak_in_flight = 0;
   int64_t completed = 0;
+  int32_t max_active = 1;
+  int64_t batched_launches = 0;  // batched Clenshaw-step launches
+  int32_t widest_batch = 0;      // most requests in one of them
   bool stop = false;
-  std::vector<std::thread> workers;
+  std::thread engine;
 };
 
 namespace {
@@ -88,67 +101,235 @@ bool admissible(const apf_server* s, const Request* r) {
   return s->running == 0 || s->in_flight + r->footprint <= s->budget;
 }
 
-void run_request(apf_server* s, Request* r) {
+// An admitted request: its context (own stream), matrix and solve.
+struct Active {
+  Request* r = nullptr;
   apf_ctx* ctx = nullptr;
-  apf_status st = apf_create(&ctx, s->device, nullptr);
-  if (st != APF_OK) {
-    r->status = st;
-    return;
-  }
   apf_matrix* A = nullptr;
-  st = apf_matrix_create_csr(ctx, r->n, r->nnz, r->rowptr.data(), r->colidx.data(), r->vals.data(), r->dtype, 0, &A);
-  apf_result* res = nullptr;
-  if (st == APF_OK) {
-    st = apf_solve(ctx, A, &r->prm, &res);
-    apf_matrix_destroy(A);
-  }
-  cudaSetDevice(s->device);
-  cudaStreamSynchronize(ctx->stream);
-  if (res) {
-    res->owns_ctx = true;
-    r->result = res;
-  } else {
-    apf_destroy(ctx);
-  }
-  r->status = st;
-  // the host copies are no longer needed
+  std::unique_ptr<apf::EngineSolve> solve;
+};
+
+void release_host_copies(Request* r) {
   std::vector<int64_t>().swap(r->rowptr);
   std::vector<int32_t>().swap(r->colidx);
   std::vector<unsigned char>().swap(r->vals);
 }
 
-void worker_main(apf_server* s, int32_t w) {
+// Ends a request: its result (or its failure) goes to the waiter.
+void finish(apf_server* s, Active& a, apf_status st, apf_result* res) {
+  if (a.A) apf_matrix_destroy(a.A);
+  a.A = nullptr;
+  a.solve.reset();
+  if (res) {
+    res->owns_ctx = true;
+    a.r->result = res;
+  } else if (a.ctx) {
+    apf_destroy(a.ctx);
+  }
+  a.ctx = nullptr;
+  a.r->status = st;
+  release_host_copies(a.r);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    a.r->t_end = Clock::now();
+    s->in_flight -= a.r->footprint;
+    s->running -= 1;
+    s->completed += 1;
+    a.r->done = true;
+  }
+  s->cv_done.notify_all();
+}
+
+// Set-up of an admitted request (ingest, bounds, coefficients, initial block).
+bool start(apf_server* s, Active& a) {
+  apf_status st = apf_create(&a.ctx, s->device, nullptr);
+  if (st == APF_OK)
+    st = apf_matrix_create_csr(a.ctx, a.r->n, a.r->nnz, a.r->rowptr.data(), a.r->colidx.data(), a.r->vals.data(),
+                               a.r->dtype, 0, &a.A);
+  if (st == APF_OK) {
+    try {
+      a.solve = apf::engine_start(a.ctx, a.A, &a.r->prm);
+    } catch (const ApfError& e) {
+      st = e.status;
+    } catch (...) {
+      st = APF_ERR_CUDA;
+    }
+  }
+  if (st != APF_OK) {
+    finish(s, a, st, nullptr);
+    return false;
+  }
+  return true;
+}
+
+// One outer iteration of every active request, the filter steps batched.
+void iterate(apf_server* s, apf_ctx* ectx, std::vector<Active>& act, std::vector<apf_status>& fail) {
+  int64_t launches = 0;
+  int32_t widest = 0;
+  auto launch = [&](bool cplx, apf::MultiArgs& ma) {
+    apf::engine_step_launch(ectx, cplx, ma);
+    launches += 1;
+    widest = std::max(widest, (int32_t)ma.nreq);
+  };
+  for (size_t i = 0; i < act.size(); ++i) {
+    try {
+      act[i].solve->begin_iteration();
+    } catch (const ApfError& e) {
+      fail[i] = e.status;
+    } catch (...) {
+      fail[i] = APF_ERR_CUDA;
+    }
+  }
+  std::vector<cudaEvent_t> evs;
+  auto event = [&]() {
+    cudaEvent_t e = nullptr;
+    APF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    evs.push_back(e);
+    return e;
+  };
+  struct EvGuard {
+    std::vector<cudaEvent_t>* v;
+    ~EvGuard() {
+      for (auto e : *v) cudaEventDestroy(e);
+    }
+  } guard{&evs};
+  int smax = 0;
+  for (size_t i = 0; i < act.size(); ++i)
+    if (fail[i] == APF_OK && act[i].solve->batched()) {
+      // the engine stream waits for the request's filter inputs
+      cudaEvent_t e = event();
+      APF_CUDA(cudaEventRecord(e, act[i].ctx->stream));
+      APF_CUDA(cudaStreamWaitEvent(ectx->stream, e, 0));
+      smax = std::max(smax, act[i].solve->steps());
+    }
+  bool engine_failed = false;
+  try {
+    for (int g = smax - 1; g >= 0; --g) {
+      for (int cplx = 0; cplx < 2; ++cplx) {
+        apf::MultiArgs ma{};
+        for (size_t i = 0; i < act.size(); ++i) {
+          auto& sv = *act[i].solve;
+          if (fail[i] != APF_OK || !sv.batched() || sv.is_complex() != (cplx == 1) || sv.steps() <= g) continue;
+          if (ma.nreq == apf::kMaxBatch) {  // a full descriptor set: launch and start another
+            launch(cplx == 1, ma);
+            ma = apf::MultiArgs{};
+          }
+          sv.step_desc(g, &ma.d[ma.nreq++]);
+        }
+        if (ma.nreq) launch(cplx == 1, ma);
+      }
+    }
+    if (smax > 0 && apf::fetch_device_error(ectx) != 0) throw ApfError{APF_ERR_TIMEOUT, "batched filter step"};
+  } catch (...) {
+    engine_failed = true;
+    cudaGetLastError();
+  }
+  if (smax > 0) {
+    cudaEvent_t done = event();
+    APF_CUDA(cudaEventRecord(done, ectx->stream));
+    for (size_t i = 0; i < act.size(); ++i)
+      if (fail[i] == APF_OK && act[i].solve->batched()) {
+        if (engine_failed) fail[i] = APF_ERR_TIMEOUT;
+        else APF_CUDA(cudaStreamWaitEvent(act[i].ctx->stream, done, 0));
+      }
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->batched_launches += launches;
+    s->widest_batch = std::max(s->widest_batch, widest);
+  }
+  // orthogonalisation and Rayleigh-Ritz of all requests, then their checks
+  for (size_t i = 0; i < act.size(); ++i) {
+    if (fail[i] != APF_OK) continue;
+    try {
+      act[i].solve->end_iteration();
+    } catch (const ApfError& e) {
+      fail[i] = e.status;
+    } catch (...) {
+      fail[i] = APF_ERR_CUDA;
+    }
+  }
+  for (size_t i = 0; i < act.size(); ++i) {
+    if (fail[i] != APF_OK) continue;
+    try {
+      act[i].solve->check();
+    } catch (const ApfError& e) {
+      fail[i] = e.status;
+    } catch (...) {
+      fail[i] = APF_ERR_CUDA;
+    }
+  }
+}
+
+void engine_main(apf_server* s) {
   cudaSetDevice(s->device);
+  apf_ctx* ectx = nullptr;
+  const apf_status est = apf_create(&ectx, s->device, nullptr);
+  std::vector<Active> act;
+  int32_t slot = 0;
   for (;;) {
-    Request* r = nullptr;
+    std::vector<Active> fresh;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_queue.wait(lk, [&] { return s->stop || (!s->queue.empty() && admissible(s, s->queue.front())); });
-      if (s->queue.empty() || !admissible(s, s->queue.front())) {
-        if (s->stop) return;
+      s->cv_queue.wait(lk, [&] { return s->stop || !s->queue.empty() || !act.empty(); });
+      while (!s->queue.empty() && (int32_t)act.size() + (int32_t)fresh.size() < s->max_active &&
+             admissible(s, s->queue.front())) {
+        Request* r = s->queue.front();
+        s->queue.pop_front();
+        s->in_flight += r->footprint;
+        s->running += 1;
+        s->peak_running = std::max(s->peak_running, s->running);
+        s->peak_in_flight = std::max(s->peak_in_flight, s->in_flight);
+        r->worker = slot++;
+        r->t_start = Clock::now();
+        Active a;
+        a.r = r;
+        fresh.push_back(std::move(a));
+      }
+      if (act.empty() && fresh.empty() && s->stop && s->queue.empty()) break;
+    }
+    for (auto& a : fresh) {
+      if (est != APF_OK) {
+        finish(s, a, est, nullptr);
         continue;
       }
-      r = s->queue.front();
-      s->queue.pop_front();
-      s->in_flight += r->footprint;
-      s->running += 1;
-      s->peak_running = std::max(s->peak_running, s->running);
-      s->peak_in_flight = std::max(s->peak_in_flight, s->in_flight);
-      r->worker = w;
-      r->t_start = Clock::now();
+      if (start(s, a)) act.push_back(std::move(a));
     }
-    run_request(s, r);
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      r->t_end = Clock::now();
-      s->in_flight -= r->footprint;
-      s->running -= 1;
-      s->completed += 1;
-      r->done = true;
+    if (act.empty()) continue;
+    std::vector<apf_status> fail(act.size(), APF_OK);
+    try {
+      iterate(s, ectx, act, fail);
+    } catch (const ApfError& e) {
+      for (auto& f : fail)
+        if (f == APF_OK) f = e.status;
+    } catch (...) {
+      for (auto& f : fail)
+        if (f == APF_OK) f = APF_ERR_CUDA;
     }
-    s->cv_done.notify_all();
+    std::vector<Active> keep;
+    for (size_t i = 0; i < act.size(); ++i) {
+      Active& a = act[i];
+      if (fail[i] != APF_OK) {
+        finish(s, a, fail[i], nullptr);
+      } else if (a.solve->finished()) {
+        apf_status st = APF_OK;
+        apf_result* res = nullptr;
+        try {
+          res = a.solve->take_result(&st);
+        } catch (const ApfError& e) {
+          st = e.status;
+        } catch (...) {
+          st = APF_ERR_CUDA;
+        }
+        finish(s, a, st, res);
+      } else {
+        keep.push_back(std::move(a));
+      }
+    }
+    act.swap(keep);
     s->cv_queue.notify_all();
   }
+  if (ectx) apf_destroy(ectx);
 }
 
 }  // namespace
@@ -157,6 +338,8 @@ extern "C" {
 
 apf_status apf_server_create(apf_server** out, int32_t device, int32_t max_concurrent, int64_t hbm_budget_bytes) {
   if (!out || max_concurrent < 1 || max_concurrent > 64 || hbm_budget_bytes < 0) return APF_ERR_ARG;
+  // active requests of one batch: up to kMaxBatch descriptors per launch and type
+  if (max_concurrent > 2 * apf::kMaxBatch) max_concurrent = 2 * apf::kMaxBatch;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
     cudaGetLastError();
@@ -175,15 +358,10 @@ apf_status apf_server_create(apf_server** out, int32_t device, int32_t max_concu
   apf_server* s = new apf_server();
   s->device = device;
   s->budget = budget;
+  s->max_active = max_concurrent;
   try {
-    for (int32_t w = 0; w < max_concurrent; ++w) s->workers.emplace_back(worker_main, s, w);
+    s->engine = std::thread(engine_main, s);
   } catch (...) {
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      s->stop = true;
-    }
-    s->cv_queue.notify_all();
-    for (auto& t : s->workers) t.join();
     delete s;
     return APF_ERR_OOM;
   }
@@ -256,11 +434,13 @@ apf_status apf_server_state(apf_server* s, apf_server_info* out) {
   out->queued = (int32_t)s->queue.size();
   out->running = s->running;
   out->peak_running = s->peak_running;
-  out->workers = (int32_t)s->workers.size();
+  out->workers = s->max_active;
   out->in_flight_bytes = s->in_flight;
   out->peak_in_flight_bytes = s->peak_in_flight;
   out->budget_bytes = s->budget;
   out->completed = s->completed;
+  out->batched_launches = s->batched_launches;
+  out->widest_batch = s->widest_batch;
   return APF_OK;
 }
 
@@ -272,7 +452,7 @@ apf_status apf_server_destroy(apf_server* s) {
     s->stop = true;
   }
   s->cv_queue.notify_all();
-  for (auto& t : s->workers) t.join();
+  if (s->engine.joinable()) s->engine.join();
   for (auto& kv : s->reqs)  // results nobody waited for
     if (kv.second->result) apf_result_destroy(kv.second->result);
   delete s;
