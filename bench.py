@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="anderson3d_c_64")
     ap.add_argument("--precision", default="f32_defect", choices=["f64", "f32", "f32_defect"])
-    ap.add_argument("--max-iter", type=int, default=60)
+    ap.add_argument("--max-iter", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1,
                     help="end-to-end solves through the C ABI from host buffers (after the timed ones)")

@@ -45,7 +45,7 @@ def _alone(B, reqs):
     res = []
     for A, prm, _ in reqs:
         M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
-        r = B.solve(ctx, M, B.default_params(**prm))
+        r = B.solve(ctx, M, B.default_params(**prm), allow_no_convergence=True)
         res.append((r.eigvals(), r.residuals(), r.stats()["iterations"]))
         r.close()
         M.close()
@@ -58,7 +58,7 @@ def _served(B, reqs, **kw):
     tickets = [srv.submit(A.n, A.rowptr, A.colidx, A.vals, B.default_params(**prm)) for A, prm, _ in reqs]
     res, infos = [], []
     for t in tickets:
-        r, info = srv.wait(t)
+        r, info = srv.wait(t, allow_no_convergence=True)
         res.append((r.eigvals(), r.residuals(), r.stats()["iterations"]))
         infos.append(info)
         r.close()
