@@ -253,18 +253,21 @@ apf_status apf_result_destroy(apf_result* r);
 /* ---- serving: many solves on one GPU -------------------------------------- */
 /* The paper solves one problem at a time; this loop serves independent
  * requests (Sec. 1: slices and problems need no communication) with
- * continuous batching on one device.  One engine thread advances every
- * admitted request's Alg. 4 in lockstep outer iterations; requests are
- * admitted in arrival order between iterations, when a slot is free and their
+ * continuous batching on one device.  One engine thread runs every admitted
+ * request's Alg. 4; each launch of the batched Clenshaw step carries the next
+ * step (Alg. 2) of every request in the filter phase of its current outer
+ * iteration (one launch for the real and one for the complex problems), so
+ * the filter steps of requests of different sizes, widths and degrees share
+ * launches.  A request whose recurrence ends runs its orthogonalisation,
+ * Rayleigh-Ritz and residual steps on its own CUDA stream, overlapping the
+ * others, and rejoins the launches with its next iteration.  Requests are
+ * admitted in arrival order between launches, when a slot is free and their
  * estimated device footprint fits in the budget left by the running ones (or
- * when none runs).  In each iteration the Clenshaw steps (Alg. 2) of all
- * running requests with an FP32 filter run together, one launch per step for
- * all real and one for all complex problems (a request of lower degree joins
- * the recurrence later; all finish on the same step); the dense steps then
- * run concurrently, one CUDA stream per request.  Each request's subspace and
- * filter state stays on the device from admission to completion.  A
- * request's arithmetic does not depend on the other requests: its result is
- * the same alone and in a mix, and the same as apf_solve's. */
+ * when none runs).  Each request's subspace and filter state stays on the
+ * device from admission to completion.  A request's arithmetic does not
+ * depend on the other requests: its result is the same alone and in a mix,
+ * and the same as apf_solve's (requests with an FP64 filter, or whose matrix
+ * has no SELL copy, filter on their own stream). */
 typedef struct apf_server apf_server;
 
 typedef struct {

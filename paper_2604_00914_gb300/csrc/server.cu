@@ -2,21 +2,21 @@
 // continuous batching.
 //
 // Requests (a Hermitian matrix in host CSR plus solver parameters) are queued
-// in arrival order.  One engine thread runs every admitted request's Alg. 4 in
-// lockstep outer iterations: the head of the queue is admitted between
-// iterations when a slot is free and its estimated device footprint fits in
-// what the running solves leave of the HBM budget (or when nothing runs), so a
-// request that arrives while others are on the GPU joins at their next
-// iteration.  In each iteration the Clenshaw steps (Alg. 2) of all running
-// requests go out together: step j of every request whose recurrence has
-// reached j runs in ONE launch (spmm_multi.cuh), real and complex problems in
-// one launch each; a request of lower degree joins the recurrence later and all
-// finish on the same step.  The orthogonalisation, Rayleigh-Ritz and residual
-// steps of the requests then run concurrently, each on its own CUDA stream.
-// Each request's state (subspace, locked vectors, filter buffers) stays on the
-// device from admission to completion.  The arithmetic of a request does not
-// depend on the other requests, so its result is the same alone and in a mix
-// (and the same as apf_solve's).
+// in arrival order.  One engine thread runs every admitted request's Alg. 4
+// and batches their filter steps: each launch of the batched Clenshaw step
+// (spmm_multi.cuh) carries the next step (Alg. 2) of every request that is in
+// the filter phase of its current outer iteration, real and complex problems
+// in one launch each.  A request whose recurrence ends queues its
+// orthogonalisation, Rayleigh-Ritz and residual steps on its own CUDA stream
+// (they overlap with the batched launches and with the other requests' dense
+// work) and rejoins the launches with its next iteration as soon as its
+// checks are done, so no request waits for another's iteration.  The head of
+// the queue is admitted between launches when a slot is free and its
+// estimated device footprint fits in what the running solves leave of the HBM
+// budget (or when nothing runs).  Each request's state (subspace, locked
+// vectors, filter buffers) stays on the device from admission to completion.
+// The arithmetic of a request does not depend on the other requests, so its
+// result is the same alone and in a mix (and the same as apf_solve's).
 //
 // The result of a request owns that request's context; apf_result_destroy
 // releases both.
@@ -101,12 +101,19 @@ bool admissible(const apf_server* s, const Request* r) {
   return s->running == 0 || s->in_flight + r->footprint <= s->budget;
 }
 
-// An admitted request: its context (own stream), matrix and solve.
+// An admitted request: its context (own stream), matrix and solve, and where
+// it stands in its current outer iteration.
 struct Active {
+  enum Phase { kFilter, kDense };
   Request* r = nullptr;
   apf_ctx* ctx = nullptr;
   apf_matrix* A = nullptr;
   std::unique_ptr<apf::EngineSolve> solve;
+  Phase phase = kDense;
+  int next_step = -1;             // next Clenshaw step (kFilter), counting down to 0
+  cudaEvent_t ready = nullptr;    // the request's filter inputs are on its stream
+  cudaEvent_t dense = nullptr;    // its orthogonalisation / Rayleigh-Ritz are done
+  apf_status fail = APF_OK;
 };
 
 void release_host_copies(Request* r) {
@@ -117,6 +124,9 @@ void release_host_copies(Request* r) {
 
 // Ends a request: its result (or its failure) goes to the waiter.
 void finish(apf_server* s, Active& a, apf_status st, apf_result* res) {
+  if (a.ready) cudaEventDestroy(a.ready);
+  if (a.dense) cudaEventDestroy(a.dense);
+  a.ready = a.dense = nullptr;
   if (a.A) apf_matrix_destroy(a.A);
   a.A = nullptr;
   a.solve.reset();
@@ -140,20 +150,53 @@ void finish(apf_server* s, Active& a, apf_status st, apf_result* res) {
   s->cv_done.notify_all();
 }
 
-// Set-up of an admitted request (ingest, bounds, coefficients, initial block).
-bool start(apf_server* s, Active& a) {
+template <class F>
+apf_status guarded(F&& f) {
+  try {
+    f();
+  } catch (const ApfError& e) {
+    return e.status;
+  } catch (...) {
+    return APF_ERR_CUDA;
+  }
+  return APF_OK;
+}
+
+// Opens an outer iteration: the filter inputs on the request's stream; with
+// batched steps to run, the engine stream will wait for them; without (FP64
+// filter, no SELL copy, degree 0 or 1) the rest of the iteration is queued now.
+void open_iteration(apf_ctx* ectx, Active& a) {
+  a.fail = guarded([&] {
+    a.solve->begin_iteration();
+    if (a.solve->batched() && a.solve->steps() > 0) {
+      APF_CUDA(cudaEventRecord(a.ready, a.ctx->stream));
+      APF_CUDA(cudaStreamWaitEvent(ectx->stream, a.ready, 0));
+      a.phase = Active::kFilter;
+      a.next_step = a.solve->steps() - 1;
+    } else {
+      a.solve->end_iteration();
+      APF_CUDA(cudaEventRecord(a.dense, a.ctx->stream));
+      a.phase = Active::kDense;
+    }
+  });
+}
+
+// Set-up of an admitted request (ingest, bounds, coefficients, initial block)
+// and its first iteration's filter inputs.
+bool start(apf_server* s, apf_ctx* ectx, Active& a) {
   apf_status st = apf_create(&a.ctx, s->device, nullptr);
   if (st == APF_OK)
     st = apf_matrix_create_csr(a.ctx, a.r->n, a.r->nnz, a.r->rowptr.data(), a.r->colidx.data(), a.r->vals.data(),
                                a.r->dtype, 0, &a.A);
-  if (st == APF_OK) {
-    try {
+  if (st == APF_OK)
+    st = guarded([&] {
+      APF_CUDA(cudaEventCreateWithFlags(&a.ready, cudaEventDisableTiming));
+      APF_CUDA(cudaEventCreateWithFlags(&a.dense, cudaEventDisableTiming));
       a.solve = apf::engine_start(a.ctx, a.A, &a.r->prm);
-    } catch (const ApfError& e) {
-      st = e.status;
-    } catch (...) {
-      st = APF_ERR_CUDA;
-    }
+    });
+  if (st == APF_OK) {
+    open_iteration(ectx, a);
+    st = a.fail;
   }
   if (st != APF_OK) {
     finish(s, a, st, nullptr);
@@ -161,118 +204,72 @@ bool start(apf_server* s, Active& a) {
   }
   return true;
 }
-
-// One outer iteration of every active request, the filter steps batched.
-void iterate(apf_server* s, apf_ctx* ectx, std::vector<Active>& act, std::vector<apf_status>& fail) {
+// One batched launch per problem type: the next Clenshaw step of every request
+// in its filter phase (at most kMaxBatch per launch).  A request whose
+// recurrence ends with this launch queues the rest of its iteration on its own
+// stream, after the launch.
+void tick(apf_server* s, apf_ctx* ectx, std::vector<Active>& act, cudaEvent_t step_done) {
   int64_t launches = 0;
   int32_t widest = 0;
-  auto launch = [&](bool cplx, apf::MultiArgs& ma) {
-    apf::engine_step_launch(ectx, cplx, ma);
-    launches += 1;
-    widest = std::max(widest, (int32_t)ma.nreq);
-  };
-  for (size_t i = 0; i < act.size(); ++i) {
-    try {
-      act[i].solve->begin_iteration();
-    } catch (const ApfError& e) {
-      fail[i] = e.status;
-    } catch (...) {
-      fail[i] = APF_ERR_CUDA;
+  for (int cplx = 0; cplx < 2; ++cplx) {
+    apf::MultiArgs ma{};
+    std::vector<size_t> members;
+    auto launch = [&]() {
+      const apf_status st = guarded([&] { apf::engine_step_launch(ectx, cplx == 1, ma); });
+      if (st != APF_OK)
+        for (size_t m : members) act[m].fail = st;
+      launches += 1;
+      widest = std::max(widest, (int32_t)ma.nreq);
+      ma = apf::MultiArgs{};
+      members.clear();
+    };
+    for (size_t i = 0; i < act.size(); ++i) {
+      Active& a = act[i];
+      if (a.fail != APF_OK || a.phase != Active::kFilter || a.solve->is_complex() != (cplx == 1)) continue;
+      if (ma.nreq == apf::kMaxBatch) launch();
+      a.solve->step_desc(a.next_step, &ma.d[ma.nreq++]);
+      a.next_step -= 1;
+      members.push_back(i);
+    }
+    if (ma.nreq) launch();
+  }
+  bool ended = false;
+  for (auto& a : act) ended = ended || (a.fail == APF_OK && a.phase == Active::kFilter && a.next_step < 0);
+  if (ended) {
+    const apf_status st = guarded([&] { APF_CUDA(cudaEventRecord(step_done, ectx->stream)); });
+    for (auto& a : act) {
+      if (a.fail != APF_OK || a.phase != Active::kFilter || a.next_step >= 0) continue;
+      a.fail = st != APF_OK ? st : guarded([&] {
+        APF_CUDA(cudaStreamWaitEvent(a.ctx->stream, step_done, 0));
+        a.solve->end_iteration();
+        APF_CUDA(cudaEventRecord(a.dense, a.ctx->stream));
+      });
+      a.phase = Active::kDense;
     }
   }
-  std::vector<cudaEvent_t> evs;
-  auto event = [&]() {
-    cudaEvent_t e = nullptr;
-    APF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    evs.push_back(e);
-    return e;
-  };
-  struct EvGuard {
-    std::vector<cudaEvent_t>* v;
-    ~EvGuard() {
-      for (auto e : *v) cudaEventDestroy(e);
-    }
-  } guard{&evs};
-  int smax = 0;
-  for (size_t i = 0; i < act.size(); ++i)
-    if (fail[i] == APF_OK && act[i].solve->batched()) {
-      // the engine stream waits for the request's filter inputs
-      cudaEvent_t e = event();
-      APF_CUDA(cudaEventRecord(e, act[i].ctx->stream));
-      APF_CUDA(cudaStreamWaitEvent(ectx->stream, e, 0));
-      smax = std::max(smax, act[i].solve->steps());
-    }
-  bool engine_failed = false;
-  try {
-    for (int g = smax - 1; g >= 0; --g) {
-      for (int cplx = 0; cplx < 2; ++cplx) {
-        apf::MultiArgs ma{};
-        for (size_t i = 0; i < act.size(); ++i) {
-          auto& sv = *act[i].solve;
-          if (fail[i] != APF_OK || !sv.batched() || sv.is_complex() != (cplx == 1) || sv.steps() <= g) continue;
-          if (ma.nreq == apf::kMaxBatch) {  // a full descriptor set: launch and start another
-            launch(cplx == 1, ma);
-            ma = apf::MultiArgs{};
-          }
-          sv.step_desc(g, &ma.d[ma.nreq++]);
-        }
-        if (ma.nreq) launch(cplx == 1, ma);
-      }
-    }
-    if (smax > 0 && apf::fetch_device_error(ectx) != 0) throw ApfError{APF_ERR_TIMEOUT, "batched filter step"};
-  } catch (...) {
-    engine_failed = true;
-    cudaGetLastError();
-  }
-  if (smax > 0) {
-    cudaEvent_t done = event();
-    APF_CUDA(cudaEventRecord(done, ectx->stream));
-    for (size_t i = 0; i < act.size(); ++i)
-      if (fail[i] == APF_OK && act[i].solve->batched()) {
-        if (engine_failed) fail[i] = APF_ERR_TIMEOUT;
-        else APF_CUDA(cudaStreamWaitEvent(act[i].ctx->stream, done, 0));
-      }
-  }
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->batched_launches += launches;
-    s->widest_batch = std::max(s->widest_batch, widest);
-  }
-  // orthogonalisation and Rayleigh-Ritz of all requests, then their checks
-  for (size_t i = 0; i < act.size(); ++i) {
-    if (fail[i] != APF_OK) continue;
-    try {
-      act[i].solve->end_iteration();
-    } catch (const ApfError& e) {
-      fail[i] = e.status;
-    } catch (...) {
-      fail[i] = APF_ERR_CUDA;
-    }
-  }
-  for (size_t i = 0; i < act.size(); ++i) {
-    if (fail[i] != APF_OK) continue;
-    try {
-      act[i].solve->check();
-    } catch (const ApfError& e) {
-      fail[i] = e.status;
-    } catch (...) {
-      fail[i] = APF_ERR_CUDA;
-    }
-  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->batched_launches += launches;
+  s->widest_batch = std::max(s->widest_batch, widest);
 }
 
+// The engine: admission between steps, one batched launch per tick for the
+// requests in their filter phase, and the requests whose dense work is done
+// moved on to their next iteration (or finished).
 void engine_main(apf_server* s) {
   cudaSetDevice(s->device);
   apf_ctx* ectx = nullptr;
   const apf_status est = apf_create(&ectx, s->device, nullptr);
+  cudaEvent_t step_done = nullptr;
+  if (est == APF_OK && cudaEventCreateWithFlags(&step_done, cudaEventDisableTiming) != cudaSuccess) step_done = nullptr;
   std::vector<Active> act;
   int32_t slot = 0;
+  int64_t ticks = 0;
   for (;;) {
     std::vector<Active> fresh;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_queue.wait(lk, [&] { return s->stop || !s->queue.empty() || !act.empty(); });
-      while (!s->queue.empty() && (int32_t)act.size() + (int32_t)fresh.size() < s->max_active &&
+      if (act.empty()) s->cv_queue.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+      while (!s->queue.empty() && (int32_t)(act.size() + fresh.size()) < s->max_active &&
              admissible(s, s->queue.front())) {
         Request* r = s->queue.front();
         s->queue.pop_front();
@@ -289,49 +286,69 @@ void engine_main(apf_server* s) {
       if (act.empty() && fresh.empty() && s->stop && s->queue.empty()) break;
     }
     for (auto& a : fresh) {
-      if (est != APF_OK) {
-        finish(s, a, est, nullptr);
+      if (est != APF_OK || !step_done) {
+        finish(s, a, est != APF_OK ? est : APF_ERR_CUDA, nullptr);
         continue;
       }
-      if (start(s, a)) act.push_back(std::move(a));
+      if (start(s, ectx, a)) act.push_back(std::move(a));
     }
     if (act.empty()) continue;
-    std::vector<apf_status> fail(act.size(), APF_OK);
-    try {
-      iterate(s, ectx, act, fail);
-    } catch (const ApfError& e) {
-      for (auto& f : fail)
-        if (f == APF_OK) f = e.status;
-    } catch (...) {
-      for (auto& f : fail)
-        if (f == APF_OK) f = APF_ERR_CUDA;
+    // a few batched steps between looks at the dense phases
+    bool filtering = false;
+    for (int t = 0; t < 8; ++t) {
+      filtering = false;
+      for (auto& a : act) filtering = filtering || (a.fail == APF_OK && a.phase == Active::kFilter);
+      if (!filtering) break;
+      tick(s, ectx, act, step_done);
+      ++ticks;
+    }
+    // a kernel of the batched launches that gave up on a wait fails the requests it served
+    if (!filtering || ticks % 256 == 0) {
+      int derr = 0;
+      const apf_status st = guarded([&] { derr = apf::fetch_device_error(ectx); });
+      if (st != APF_OK || derr != 0)
+        for (auto& a : act)
+          if (a.fail == APF_OK) a.fail = st != APF_OK ? st : APF_ERR_TIMEOUT;
+    }
+    bool progressed = false;
+    for (auto& a : act) {
+      if (a.fail != APF_OK || a.phase != Active::kDense) continue;
+      const cudaError_t q = cudaEventQuery(a.dense);
+      if (q == cudaErrorNotReady) continue;
+      progressed = true;
+      if (q != cudaSuccess) {
+        cudaGetLastError();
+        a.fail = APF_ERR_CUDA;
+        continue;
+      }
+      a.fail = guarded([&] { a.solve->check(); });
+      if (a.fail == APF_OK && !a.solve->finished()) open_iteration(ectx, a);
+    }
+    if (!filtering && !progressed) {  // nothing to launch: wait for a dense phase instead of spinning
+      for (auto& a : act)
+        if (a.fail == APF_OK && a.phase == Active::kDense) {
+          cudaEventSynchronize(a.dense);
+          break;
+        }
     }
     std::vector<Active> keep;
-    for (size_t i = 0; i < act.size(); ++i) {
-      Active& a = act[i];
-      if (fail[i] != APF_OK) {
-        finish(s, a, fail[i], nullptr);
-      } else if (a.solve->finished()) {
+    for (auto& a : act) {
+      if (a.fail != APF_OK) {
+        finish(s, a, a.fail, nullptr);
+      } else if (a.phase == Active::kDense && a.solve->finished()) {
         apf_status st = APF_OK;
         apf_result* res = nullptr;
-        try {
-          res = a.solve->take_result(&st);
-        } catch (const ApfError& e) {
-          st = e.status;
-        } catch (...) {
-          st = APF_ERR_CUDA;
-        }
-        finish(s, a, st, res);
+        const apf_status g = guarded([&] { res = a.solve->take_result(&st); });
+        finish(s, a, g != APF_OK ? g : st, res);
       } else {
         keep.push_back(std::move(a));
       }
     }
     act.swap(keep);
-    s->cv_queue.notify_all();
   }
+  if (step_done) cudaEventDestroy(step_done);
   if (ectx) apf_destroy(ectx);
 }
-
 }  // namespace
 
 extern "C" {
