@@ -53,6 +53,21 @@ struct Request {
   bool claimed = false;  // a thread waits for it (a ticket can be waited for once)
 };
 
+// An admitted request: its context (own stream), matrix and solve, and where
+// it stands in its current outer iteration.
+struct Active {
+  enum Phase { kFilter, kDense };
+  Request* r = nullptr;
+  apf_ctx* ctx = nullptr;
+  apf_matrix* A = nullptr;
+  std::unique_ptr<apf::EngineSolve> solve;
+  Phase phase = kDense;
+  int next_step = -1;             // next Clenshaw step (kFilter), counting down to 0
+  cudaEvent_t ready = nullptr;    // the request's filter inputs are on its stream
+  cudaEvent_t dense = nullptr;    // its orthogonalisation / Rayleigh-Ritz are done
+  apf_status fail = APF_OK;
+};
+
 double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
 }
@@ -76,6 +91,11 @@ struct apf_server {
   int32_t widest_batch = 0;      // most requests in one of them
   bool stop = false;
   std::thread engine;
+  // set-up of admitted requests runs on threads of its own; the engine
+  // thread picks the requests up when they are ready
+  std::vector<std::thread> setups;
+  std::vector<std::unique_ptr<Active>> ready;
+  int32_t pending_setup = 0;
 };
 
 namespace {
@@ -100,21 +120,6 @@ int64_t footprint(int64_t n, int64_t nnz, int32_t dtype, int64_t p, bool gram_tc
 bool admissible(const apf_server* s, const Request* r) {
   return s->running == 0 || s->in_flight + r->footprint <= s->budget;
 }
-
-// An admitted request: its context (own stream), matrix and solve, and where
-// it stands in its current outer iteration.
-struct Active {
-  enum Phase { kFilter, kDense };
-  Request* r = nullptr;
-  apf_ctx* ctx = nullptr;
-  apf_matrix* A = nullptr;
-  std::unique_ptr<apf::EngineSolve> solve;
-  Phase phase = kDense;
-  int next_step = -1;             // next Clenshaw step (kFilter), counting down to 0
-  cudaEvent_t ready = nullptr;    // the request's filter inputs are on its stream
-  cudaEvent_t dense = nullptr;    // its orthogonalisation / Rayleigh-Ritz are done
-  apf_status fail = APF_OK;
-};
 
 void release_host_copies(Request* r) {
   std::vector<int64_t>().swap(r->rowptr);
@@ -181,29 +186,34 @@ void open_iteration(apf_ctx* ectx, Active& a) {
   });
 }
 
-// Set-up of an admitted request (ingest, bounds, coefficients, initial block)
-// and its first iteration's filter inputs.
-bool start(apf_server* s, apf_ctx* ectx, Active& a) {
-  apf_status st = apf_create(&a.ctx, s->device, nullptr);
+// Set-up of an admitted request (ingest, bounds, coefficients, subspace size,
+// initial block) on a thread of its own, so that the engine keeps launching
+// the running requests' steps meanwhile; the request then waits in `ready`.
+void setup_job(apf_server* s, Active* a) {
+  cudaSetDevice(s->device);
+  apf_status st = apf_create(&a->ctx, s->device, nullptr);
   if (st == APF_OK)
-    st = apf_matrix_create_csr(a.ctx, a.r->n, a.r->nnz, a.r->rowptr.data(), a.r->colidx.data(), a.r->vals.data(),
-                               a.r->dtype, 0, &a.A);
+    st = apf_matrix_create_csr(a->ctx, a->r->n, a->r->nnz, a->r->rowptr.data(), a->r->colidx.data(),
+                               a->r->vals.data(), a->r->dtype, 0, &a->A);
   if (st == APF_OK)
     st = guarded([&] {
-      APF_CUDA(cudaEventCreateWithFlags(&a.ready, cudaEventDisableTiming));
-      APF_CUDA(cudaEventCreateWithFlags(&a.dense, cudaEventDisableTiming));
-      a.solve = apf::engine_start(a.ctx, a.A, &a.r->prm);
+      APF_CUDA(cudaEventCreateWithFlags(&a->ready, cudaEventDisableTiming));
+      APF_CUDA(cudaEventCreateWithFlags(&a->dense, cudaEventDisableTiming));
+      a->solve = apf::engine_start(a->ctx, a->A, &a->r->prm);
     });
-  if (st == APF_OK) {
-    open_iteration(ectx, a);
-    st = a.fail;
-  }
+  std::unique_ptr<Active> own(a);
   if (st != APF_OK) {
-    finish(s, a, st, nullptr);
-    return false;
+    finish(s, *a, st, nullptr);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->pending_setup -= 1;
+  } else {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->ready.push_back(std::move(own));
+    s->pending_setup -= 1;
   }
-  return true;
+  s->cv_queue.notify_all();
 }
+
 // One batched launch per problem type: the next Clenshaw step of every request
 // in its filter phase (at most kMaxBatch per launch).  A request whose
 // recurrence ends with this launch queues the rest of its iteration on its own
@@ -265,12 +275,18 @@ void engine_main(apf_server* s) {
   int32_t slot = 0;
   int64_t ticks = 0;
   for (;;) {
-    std::vector<Active> fresh;
+    std::vector<std::unique_ptr<Active>> picked;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      if (act.empty()) s->cv_queue.wait(lk, [&] { return s->stop || !s->queue.empty(); });
-      while (!s->queue.empty() && (int32_t)(act.size() + fresh.size()) < s->max_active &&
-             admissible(s, s->queue.front())) {
+      auto in_flight = [&] { return (int32_t)act.size() + s->pending_setup + (int32_t)s->ready.size(); };
+      auto can_admit = [&] {
+        return !s->queue.empty() && in_flight() < s->max_active && admissible(s, s->queue.front());
+      };
+      if (act.empty())
+        s->cv_queue.wait(lk, [&] {
+          return !s->ready.empty() || can_admit() || (s->stop && s->queue.empty() && s->pending_setup == 0);
+        });
+      while (can_admit() && est == APF_OK && step_done) {
         Request* r = s->queue.front();
         s->queue.pop_front();
         s->in_flight += r->footprint;
@@ -279,18 +295,30 @@ void engine_main(apf_server* s) {
         s->peak_in_flight = std::max(s->peak_in_flight, s->in_flight);
         r->worker = slot++;
         r->t_start = Clock::now();
-        Active a;
-        a.r = r;
-        fresh.push_back(std::move(a));
+        auto* a = new Active();
+        a->r = r;
+        s->pending_setup += 1;
+        s->setups.emplace_back(setup_job, s, a);
       }
-      if (act.empty() && fresh.empty() && s->stop && s->queue.empty()) break;
+      picked.swap(s->ready);
+      if (act.empty() && picked.empty() && s->pending_setup == 0 && s->stop && s->queue.empty()) break;
+      if (est != APF_OK || !step_done) {  // no engine: fail what is queued
+        while (!s->queue.empty()) {
+          Request* r = s->queue.front();
+          s->queue.pop_front();
+          s->in_flight += r->footprint;
+          s->running += 1;
+          Active a;
+          a.r = r;
+          lk.unlock();
+          finish(s, a, est != APF_OK ? est : APF_ERR_CUDA, nullptr);
+          lk.lock();
+        }
+      }
     }
-    for (auto& a : fresh) {
-      if (est != APF_OK || !step_done) {
-        finish(s, a, est != APF_OK ? est : APF_ERR_CUDA, nullptr);
-        continue;
-      }
-      if (start(s, ectx, a)) act.push_back(std::move(a));
+    for (auto& p : picked) {
+      open_iteration(ectx, *p);
+      act.push_back(std::move(*p));
     }
     if (act.empty()) continue;
     // a few batched steps between looks at the dense phases
@@ -346,6 +374,8 @@ void engine_main(apf_server* s) {
     }
     act.swap(keep);
   }
+  for (auto& t : s->setups)
+    if (t.joinable()) t.join();
   if (step_done) cudaEventDestroy(step_done);
   if (ectx) apf_destroy(ectx);
 }
