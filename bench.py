@@ -75,7 +75,11 @@ def parse():
     ap.add_argument("--requests", type=int, default=24, help="serving workload: number of requests")
     ap.add_argument("--compare-single", action="store_true",
                     help="slice workloads: also solve the slices one after another")
-    ap.add_argument("--concurrency", type=int, default=4, help="serving workload: worker slots")
+    ap.add_argument("--concurrency", type=int, default=4, help="serving workload: requests in flight")
+    ap.add_argument("--n-hi", type=float, default=1e5, help="serving workload: largest matrix size")
+    ap.add_argument("--count-hi", type=int, default=64, help="serving workload: largest target count")
+    ap.add_argument("--burst-concurrency", type=int, default=16,
+                    help="serving workload: requests in flight in the saturated (all at once) run; 0 skips it")
     return ap.parse_args()
 
 
@@ -469,7 +473,7 @@ def serving_arm(args, dist):
     if dist.rank != 0:
         return
     torch.cuda.set_device(dist.local)
-    reqs = workloads.serving_requests(args.requests)
+    reqs = workloads.serving_requests(args.requests, n_hi=args.n_hi, count_hi=args.count_hi)
     mats = [r.matrix() for r in reqs]
     prms = [B.default_params(a=r.a, b=r.b, p=0, seed=r.seed, filter_precision=B.APF_FILTER_F32_DEFECT,
                              max_iter=args.max_iter) for r in reqs]
@@ -516,6 +520,28 @@ def serving_arm(args, dist):
     wall = time.perf_counter() - t0
     state = srv.state()
     srv.close()
+    # saturated: every request submitted at once, the makespan against the serial total
+    burst = None
+    if args.burst_concurrency > 0:
+        srv = B.Server(dist.local, max_concurrent=args.burst_concurrency)
+        tb = time.perf_counter()
+        tks = [srv.submit(A.n, A.rowptr, A.colidx, A.vals, prms[i]) for i, A in enumerate(mats)]
+        blat, bsame = [], 0
+        for i, t in enumerate(tks):
+            res, info = srv.wait(t, allow_no_convergence=True)
+            blat.append(info["latency_ms"])
+            if res is not None:
+                bsame += int(serial_lam[i] is not None and np.array_equal(serial_lam[i], res.eigvals()))
+                res.close()
+        makespan = time.perf_counter() - tb
+        bst = srv.state()
+        srv.close()
+        burst = {"concurrency": args.burst_concurrency, "makespan_s": makespan,
+                 "serial_total_s": serial_s * len(mats), "speedup_vs_serial": serial_s * len(mats) / makespan,
+                 "throughput_requests_per_s": len(mats) / makespan, "p50_ms": float(np.percentile(blat, 50)),
+                 "p99_ms": float(np.percentile(blat, 99)), "same_as_serial": bsame,
+                 "batched_launches": bst["batched_launches"], "widest_batch": bst["widest_batch"],
+                 "peak_running": bst["peak_running"]}
     clocks = sampler.stop()
     lat = np.array(lat)
     print(json.dumps({
@@ -527,8 +553,10 @@ def serving_arm(args, dist):
         "arrival_rate_per_s": rate, "throughput_requests_per_s": len(reqs) / wall,
         "eigenpairs_per_s": eig / wall, "concurrency": args.concurrency,
         "peak_running": state["peak_running"], "peak_in_flight_bytes": state["peak_in_flight_bytes"],
+        "batched_launches": state["batched_launches"], "widest_batch": state["widest_batch"],
+        "saturated": burst,
         "data": "synthetic", "clocks": clocks,
-        "config": {"workload": "serving", "n_range": [1e4, 1e5], "target_counts": [8, 64],
+        "config": {"workload": "serving", "n_range": [1e4, args.n_hi], "target_counts": [8, args.count_hi],
                    "p": "estimated (Sec. 3.4)", "precision": "f32_defect"}}), flush=True)
 
 

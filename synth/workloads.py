@@ -211,10 +211,10 @@ class Request:
 
 
 def serving_requests(count: int = 24, seed: int = BASE_SEED + 5, n_lo: float = 1e4,
-                     n_hi: float = 1e5) -> list:
+                     n_hi: float = 1e5, count_hi: int = 64) -> list:
     """A seeded stream of independent eigenproblems: Anderson models in 2D or
     3D (50/50), real or complex (50/50), n log-uniform in [n_lo, n_hi]
-    (L = round(n^(1/d))), disorder W ~ U[1, 6], a target count U{8..64} and an
+    (L = round(n^(1/d))), disorder W ~ U[1, 6], a target count U{8..count_hi} and an
     interval of that many states under a flat density of states over the
     Gershgorin range [-2d - W/2, 2d + W/2], centred uniformly in the middle
     half of the band.  The true count differs from the target where the
@@ -230,7 +230,7 @@ def serving_requests(count: int = 24, seed: int = BASE_SEED + 5, n_lo: float = 1
         n = math.exp(math.log(n_lo) + u[i, 2] * (math.log(n_hi) - math.log(n_lo)))
         L = max(3, int(round(n ** (1.0 / dim))))
         W = 1.0 + 5.0 * u[i, 3]
-        target = 8 + int(57 * u[i, 4])
+        target = 8 + int((count_hi - 7) * u[i, 4])
         span = 4.0 * dim + W
         half = 0.5 * target * span / (L ** dim)
         centre = (u[i, 5] - 0.5) * 0.5 * span

@@ -104,6 +104,29 @@ def test_slices_match_definition(B, ctx, prec, is_complex):
     _check_against_definition(out, A, lam, a, b)
 
 
+@pytest.mark.slow
+def test_wide_slices_beyond_1024_columns(B, ctx):
+    """Twelve slices whose subspaces add up to more than 1024 columns (the
+    batched filter then runs in column tiles): every slice as the definition
+    gives it.  Real 3D Anderson model, 16^3."""
+    A = matrices.anderson(16, 3, 5.0, 23, False)
+    lam = np.linalg.eigvalsh(A.to_dense())
+    specs = [(200 + 160 * s, 60 + 5 * (s % 3)) for s in range(12)]
+    a, b = _slices(lam, specs)
+    p = np.array([c + 36 for _, c in specs])
+    assert p.sum() > 1024
+    out = _run_slices(B, ctx, A, a, b, p, 5, filter_precision=B.APF_FILTER_F32_DEFECT)
+    assert out["stats"]["p_used"] == p.sum()
+    ref_counts = [int(np.sum((lam >= lo) & (lam <= hi))) for lo, hi in zip(a, b)]
+    assert list(out["counts"]) == ref_counts
+    inside = np.zeros(lam.size, bool)
+    for lo, hi in zip(a, b):
+        inside |= (lam >= lo) & (lam <= hi)
+    assert np.max(np.abs(out["lam"] - lam[inside])) <= 1e-10 * np.abs(lam).max()
+    res = np.linalg.norm(A.to_scipy() @ out["V"] - out["V"] * out["lam"], axis=0)
+    assert res.max() <= 1e-10 * np.abs(lam).max()
+
+
 @pytest.mark.parametrize("prec", PREC)
 def test_slices_equal_single_solves(B, ctx, prec):
     """Each slice finds the eigenvalues a single solve of its interval finds,
