@@ -266,8 +266,10 @@ apf_status apf_result_destroy(apf_result* r);
  * when none runs).  Each request's subspace and filter state stays on the
  * device from admission to completion.  A request's arithmetic does not
  * depend on the other requests: its result is the same alone and in a mix,
- * and the same as apf_solve's (requests with an FP64 filter, or whose matrix
- * has no SELL copy, filter on their own stream). */
+ * and the same as apf_solve's.  Requests large enough to fill the GPU with
+ * their own steps (at least eight 32-row tiles of the step per SM), with an
+ * FP64 filter, or whose matrix has no SELL copy filter on their own stream,
+ * concurrently with the batched launches. */
 typedef struct apf_server apf_server;
 
 typedef struct {

@@ -49,7 +49,7 @@ class EngineSolveT final : public EngineSolve {
     st.lambda_max = bd.lmax;
     st.norm_a = bd.normA;
     fs.init(ctx, A, S.ld, bd.l1, bd.l2, S.coef, prm.filter_precision);
-    fs.graphs_on = false;
+    fs.graphs_on = prm.filter_graphs != 0;  // for the iterations it filters on its own
     APF_CUDA(cudaStreamSynchronize(ctx->stream));
     st.ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   }
@@ -62,10 +62,14 @@ class EngineSolveT final : public EngineSolve {
     k = S.ki;
     const int64_t n = A->n, p = S.pa, ld = S.ld;
     defect = S.have_ritz && prm.filter_precision == APF_FILTER_F32_DEFECT;
-    batched_ = prm.filter_precision != APF_FILTER_F64 && A->sell_ok;
+    // batch the steps of problems too small to fill the GPU alone (fewer tiles
+    // of the batched step than eight per SM); larger ones, FP64 filters and
+    // matrices without a SELL copy filter on their own stream, concurrently
+    const int64_t tiles = ((n + 31) / 32) * (((p + E - 1) / E + 15) / 16);
+    batched_ = prm.filter_precision != APF_FILTER_F64 && A->sell_ok && tiles < 8LL * ctx->num_sms;
     nsteps = 0;
     result = nullptr;
-    if (!batched_) {  // FP64 filter, or no SELL copy: this request's filter runs on its own
+    if (!batched_) {  // this request filters on its own stream
       fs.apply(k, S.Vh.template as<T>(), defect ? S.AVh.template as<T>() : nullptr, defect ? S.w : nullptr, p,
                S.X.template as<T>(), nullptr, nullptr, &fc);
       return;
