@@ -241,7 +241,7 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
     }
   }
   if (A->sell_ok) {
-    // column tiles: the shapes with at most 25 % idle slots, or the least idle one
+    // column tiles: the shapes with at most 50 % idle slots, or the least idle one
     int least = -1;
     for (int i = 0; i < kNumSellCtShapes; ++i) {
       const int g = kSellCtShapes[i].G, v = kSellCtShapes[i].VPT;
@@ -252,7 +252,7 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
     for (int i = 0; i < kNumSellCtShapes; ++i) {
       const int g = kSellCtShapes[i].G, v = kSellCtShapes[i].VPT;
       if (!sell_ct_fits(st, g, v, nvec)) continue;
-      if (ct_idle(g, v, nvec) > 0.25 && i != least) continue;
+      if (ct_idle(g, v, nvec) > 0.5 && i != least) continue;
       cands.push_back({4, g, v});
     }
   }
