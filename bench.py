@@ -43,8 +43,14 @@ WORK_PROFILE = {"anderson3d_c_64": {"iterations": 30, "degree_width": 22.1e6, "e
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32
 # Clenshaw step at full width (both V and Y terms), mean of three launches of
-# one ncu capture of the kernel (profiles/clenshaw_sell_traffic_<workload>.md).
-TRAFFIC_BYTES = {"anderson3d_c_64": 1.3486e9}
+# one ncu capture of the kernel (profiles/clenshaw_sell_traffic_<workload>.md),
+# keyed by workload and step kernel kind: a line whose solve picked another
+# kernel reports no traffic.
+TRAFFIC_BYTES = {("anderson3d_c_64", 1): 1.3486e9}
+
+# the FP32 step kernels (apf_matrix_set_filter_kernel kinds)
+KERNEL_NAMES = {1: "SELL-8", 2: "SELL-8 two-step", 3: "CSR", 4: "SELL-8 column-tiled",
+                5: "SELL-8 column-tiled, near rows staged"}
 
 
 def parse():
@@ -56,6 +62,8 @@ def parse():
     ap.add_argument("--workload", default="anderson3d_c_64")
     ap.add_argument("--precision", default="f32_defect", choices=["f64", "f32", "f32_defect"])
     ap.add_argument("--max-iter", type=int, default=100)
+    ap.add_argument("--filter-graphs", type=int, default=1,
+                    help="1: recurring filter applications replayed as CUDA graphs; 0: plain launches")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1,
                     help="end-to-end solves through the C ABI from host buffers (after the timed ones)")
@@ -70,6 +78,8 @@ def parse():
     ap.add_argument("--dense-only", type=int, default=0,
                     help="time N tensor-core Gram products X^H X and N block updates X M on the workload's "
                          "n x p block instead of solves")
+    ap.add_argument("--shape", default="0,0",
+                    help="filter-only mode: step kernel shape 'G,VPT' (lanes per row, vectors per lane; 0,0 = default)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="filter-only: pin the step kernel (0 autotune, 1 SELL, 2 SELL two-step, 3 CSR)")
     ap.add_argument("--requests", type=int, default=24, help="serving workload: number of requests")
@@ -267,7 +277,7 @@ def ours_arm(args, dist):
     prec = {"f64": B.APF_FILTER_F64, "f32": B.APF_FILTER_F32, "f32_defect": B.APF_FILTER_F32_DEFECT}[args.precision]
     p_used = w.p if args.p < 0 else args.p
     prm = B.default_params(a=w.a, b=w.b, p=p_used, seed=w.seed + 1000 * dist.rank, filter_precision=prec,
-                           max_iter=args.max_iter)
+                           max_iter=args.max_iter, filter_graphs=args.filter_graphs)
     peak, peak_kind = measured_peaks()
 
     def one_solve():
@@ -297,6 +307,7 @@ def ours_arm(args, dist):
     iters = 0
     maxres = 0.0
     p_stat = deg_seq = None
+    step_kernel = (-1, 0, 0)
     stage = {"setup": 0.0, "filter": 0.0, "orth_rr": 0.0, "check": 0.0, "total": 0.0}
     for _ in range(args.steps):
         e, st, hist = one_solve()
@@ -314,6 +325,7 @@ def ours_arm(args, dist):
         deg_width += sum(h["degree"] * h["width"] for h in hist)
         iters += st["iterations"]
         maxres = max(maxres, st["max_residual"])
+        step_kernel = (st["filter_kind"], st["filter_g"], st["filter_vpt"])
     ev1.record(stream)
     torch.cuda.synchronize()
     dist.barrier()
@@ -369,7 +381,8 @@ def ours_arm(args, dist):
     kind = "complex" if A.is_complex else "real"
     bits = {"f64": "FP64", "f32": "FP32", "f32_defect": "FP32"}[args.precision]
     blk_mb = A.n * w.p * (8 if A.is_complex else 4) / 1e6
-    traffic = TRAFFIC_BYTES.get(args.workload) if args.precision != "f64" and args.p < 0 else None
+    traffic = (TRAFFIC_BYTES.get((args.workload, step_kernel[0]))
+               if args.precision != "f64" and args.p < 0 else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -384,7 +397,9 @@ def ours_arm(args, dist):
                    "stage_ms_per_solve": {k_: round(v_, 1) for k_, v_ in stage.items()},
                    "l2": f"inputs larger than L2 (FP32 block {blk_mb:.0f} MB, FP64 block {2 * blk_mb:.0f} MB)",
                    "parallelism": f"replicas{args.gpus}"},
-        "roofline": {"kernel": f"Clenshaw filter step ({bits} {kind}, SELL-8)", "bound": "hbm",
+        "roofline": {"kernel": f"Clenshaw filter step ({bits} {kind}, {KERNEL_NAMES.get(step_kernel[0], 'FP64 CSR')})",
+                     "step_kernel": {"kind": step_kernel[0], "G": step_kernel[1], "VPT": step_kernel[2]},
+                     "bound": "hbm",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,
                      "traffic": traffic,
@@ -722,7 +737,8 @@ def filter_only(args, dist, B, ctx, M, A, w, peak, peak_kind):
     import torch
     from synth import rng
     n, p = A.n, w.p
-    M.set_filter_kernel(args.kernel)
+    g_, v_ = (int(t) for t in args.shape.split(","))
+    M.set_filter_kernel(args.kernel, g_, v_)
     X = torch.from_numpy(rng.uniform_block(w.seed, rng.STREAM_INIT_BLOCK, n, p, A.is_complex)).cuda()
     Y = torch.empty_like(X)
     coef = np.linspace(1.0, 0.1, args.degree + 1)
@@ -770,7 +786,7 @@ def dense_only(args, dist, B, ctx, A, w, stream):
     torch.cuda.synchronize()
     gram_ms = ev[0].elapsed_time(ev[1]) / args.dense_only
     upd_ms = ev[1].elapsed_time(ev[2]) / args.dense_only
-    chunk_flops = 28 * 2 * 2 * 128 * 32 * 32
+    chunk_flops = 28 * 2 * 128 * 32 * 32  # 28 pairs x (2 flops x M 128 x N 32 x K 32)
     pP, nP = 128 * math.ceil(p / 128), 32 * math.ceil(p / 32)
     gram_tiles = (pP // 128) * (C * nP // 32)
     gram_mma = gram_tiles * (C * 32 * math.ceil(n / 32) // 32) * chunk_flops

@@ -123,6 +123,10 @@ typedef struct {
   double filter_step_bytes;  /* algorithmic bytes of the same steps run one per launch */
   double trace_estimate;     /* estimated eigenvalue count e~ (sum over slices), 0 if p was given */
   int64_t p_used;            /* subspace size used (sum over slices) */
+  int32_t filter_kind;       /* FP32 Clenshaw step kernel of the first filter application (kinds as in
+                                apf_matrix_set_filter_kernel, CSR reported as 3); -1 for the FP64 filter
+                                and for a served request whose steps all ran in the batched launch */
+  int32_t filter_g, filter_vpt;  /* its shape: lanes per row, 16-byte vectors per lane */
 } apf_stats;
 
 #define APF_MAX_P 1024
@@ -194,10 +198,13 @@ apf_status apf_matrix_destroy(apf_matrix* A);
  * launch; 2 = SELL-8, two steps per pass over a banded (reverse Cuthill-McKee)
  * copy; 3 = CSR; 4 = SELL-8 with the block cut into column tiles of G x VPT
  * vectors, one tile per CTA, swept tile after tile (any width; the tile width
- * is what keeps the far neighbours' rows of W in L2).  (G, VPT) = lanes per
- * row x 16-byte vectors per lane, (0, 0) for the shape with the fewest idle
- * lanes.  Where a pinned kind does not apply (matrix, width) it falls back
- * 4 -> 1, 2 -> 1 -> 3.  APF_ERR_ARG for a kind outside 0..4. */
+ * is what keeps the far neighbours' rows of W in L2); 5 = as 4, with the rows
+ * of W within H rows of a CTA's own staged in shared memory (H, up to 16, is
+ * chosen at ingest from the entries near the diagonal: 4 for the 25-point
+ * stencil of an eighth-order 3D Laplacian).  (G, VPT) = lanes per row x
+ * 16-byte vectors per lane, (0, 0) for the shape with the fewest idle lanes.
+ * Where a pinned kind does not apply (matrix, width) it falls back
+ * 5 -> 4 -> 1, 2 -> 1 -> 3.  APF_ERR_ARG for a kind outside 0..5. */
 apf_status apf_matrix_set_filter_kernel(apf_matrix* A, int32_t kind, int32_t G, int32_t VPT);
 apf_status apf_matrix_info(const apf_matrix* A, int64_t* n, int64_t* nnz, int32_t* dtype);
 

@@ -71,6 +71,7 @@ class apf_stats(C.Structure):
         ("max_residual", C.c_double),
         ("filter_steps", C.c_int64), ("filter_step_bytes", C.c_double),
         ("trace_estimate", C.c_double), ("p_used", C.c_int64),
+        ("filter_kind", C.c_int32), ("filter_g", C.c_int32), ("filter_vpt", C.c_int32),
     ]
 
     def as_dict(self):
@@ -288,7 +289,9 @@ class Matrix:
         return cls(ctx, h, int(n), dt)
 
     def set_filter_kernel(self, kind, G=0, VPT=0):
-        """Pin the FP32 Clenshaw step kernel (0 = autotune, 1 = SELL, 2 = SELL two-step, 3 = CSR)."""
+        """Pin the FP32 Clenshaw step kernel (0 = autotune, 1 = SELL, 2 = SELL two-step, 3 = CSR,
+        4 = SELL column-tiled, 5 = column-tiled with near rows in shared memory); (G, VPT) = lanes per
+        row x 16-byte vectors per lane, (0, 0) = default."""
         self.ctx.lib.check(self.ctx.lib.apf_matrix_set_filter_kernel(self.h, int(kind), int(G), int(VPT)))
 
     def close(self):

@@ -80,6 +80,7 @@ struct apf_matrix {
   int32_t* sell_col = nullptr;
   int32_t* sell_src = nullptr;
   int64_t sell_bw = 0;           // max |i - j| (natural row order)
+  int sell_halo = 0;             // near-row reach H of the column-tiled step with staged W rows (0: none)
   // a second SELL-8 copy in reverse Cuthill-McKee row order, for the two-step
   // filter pass (null when the natural order is already banded)
   int32_t* perm = nullptr;       // new -> old
@@ -91,7 +92,8 @@ struct apf_matrix {
   int64_t psell_slots = 0;
   int64_t psell_bw = 0;
   // autotuned Clenshaw-step shape per (element size, vectors per row):
-  // value = kind * 10000 + G * 100 + VPT, kind 1 = SELL, 2 = SELL two-step, 0 = CSR
+  // value = kind * 10000 + G * 100 + VPT, kind 1 = SELL, 2 = SELL two-step, 4 / 5 = SELL column
+  // tiles (5: near rows of W in shared memory), 0 = CSR
   std::vector<std::pair<int64_t, int>> tune_cache;
   // a pinned kernel (apf_matrix_set_filter_kernel): kind 0 = autotune
   int pin_kind = 0, pin_G = 0, pin_VPT = 0;
@@ -151,14 +153,15 @@ void clenshaw_step_sell(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* 
                         typename ScalarTraits<T>::Real coef_scalar,
                         typename ScalarTraits<T>::Real alpha, T* Out);
 // The same step with the block cut into column tiles of G x VPT vectors, one
-// tile per CTA (grid: row ranges x tiles); any width.  See spmm_sell_ct.cuh.
+// tile per CTA (grid: row ranges x tiles); any width.  halo > 0: the rows of W
+// within halo rows of a CTA's own come from shared memory.  See spmm_sell_ct.cuh.
 template <class T, class TA>
 void clenshaw_step_sell_ct(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_t* chunk_ptr,
                            const int32_t* scol, const TA* sval, int lmax, const T* W, const T* Vin,
                            const T* Y, int64_t ld, int64_t ncols,
                            const typename ScalarTraits<T>::Real* coef_col,
                            typename ScalarTraits<T>::Real coef_scalar,
-                           typename ScalarTraits<T>::Real alpha, T* Out);
+                           typename ScalarTraits<T>::Real alpha, T* Out, int halo);
 // Two consecutive Clenshaw steps in one pass (SELL-8, temporal blocking):
 // bufB = 2 A W - va + f1 Y with W = bufA, then bufA = 2 A bufB - bufA + f2 Y.
 // bandwidth: max |i - j| of the stored pattern; seg_count / pass: see spmm_sell.cuh.

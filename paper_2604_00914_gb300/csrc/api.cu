@@ -270,9 +270,30 @@ static void ingest_csr(apf_ctx* ctx, int64_t n, const std::vector<int64_t>& rp_i
   // that at least halves the bandwidth max |i - j| (a small bandwidth lets the
   // filter run two steps per pass out of L2).
   int64_t bw0 = 0;
+  constexpr int kNearMax = 16;
+  int64_t near[kNearMax + 1] = {0};  // entries at each distance |i - j| <= kNearMax
   for (int64_t i = 0; i < n; ++i)
-    for (int64_t e = rp[(size_t)i]; e < rp[(size_t)i + 1]; ++e)
-      bw0 = std::max<int64_t>(bw0, std::abs((int64_t)ci[(size_t)e] - i));
+    for (int64_t e = rp[(size_t)i]; e < rp[(size_t)i + 1]; ++e) {
+      const int64_t dist = std::abs((int64_t)ci[(size_t)e] - i);
+      bw0 = std::max<int64_t>(bw0, dist);
+      if (dist <= kNearMax) ++near[dist];
+    }
+  // Near-row reach of the column-tiled step: a CTA of 32 rows that stages rows
+  // r0 - H .. r0 + 32 + H of W reads the entries within H of the diagonal from
+  // shared memory at the cost of (32 + 2 H) / 32 staged rows per row; keep the
+  // H in {1, 2, 4, 8, 16} that saves the most row reads, if it saves at least
+  // one per row.
+  int halo = 0;
+  {
+    double best = 1.0;
+    int64_t within = near[0];
+    for (int h = 1; h <= kNearMax; ++h) {
+      within += near[h];
+      if ((h & (h - 1)) != 0) continue;
+      const double saved = (n > 0 ? (double)within / (double)n : 0.0) - (32.0 + 2.0 * h) / 32.0;
+      if (saved > best + 1e-12) { best = saved; halo = h; }
+    }
+  }
   std::vector<int32_t> perm, iperm;  // perm: new -> old, iperm: old -> new
   int64_t bw = bw0;
   if (bw0 > 4096 && n < INT32_MAX) {
@@ -366,6 +387,7 @@ static void ingest_csr(apf_ctx* ctx, int64_t n, const std::vector<int64_t>& rp_i
       A->sell_lmax = nat.lmax;
       A->sell_slots = nat.slots;
       A->sell_bw = bw0;
+      A->sell_halo = halo;
       APF_CUDA(cudaMalloc(&A->sell_chunk_ptr, nat.cptr.size() * sizeof(int64_t)));
       APF_CUDA(cudaMalloc(&A->sell_col, std::max<size_t>(nat.col.size(), 1) * sizeof(int32_t)));
       APF_CUDA(cudaMalloc(&A->sell_src, std::max<size_t>(nat.src.size(), 1) * sizeof(int32_t)));
@@ -577,7 +599,7 @@ apf_status apf_result_slice_counts(const apf_result* r, int32_t nslices, int64_t
 }
 
 apf_status apf_matrix_set_filter_kernel(apf_matrix* A, int32_t kind, int32_t G, int32_t VPT) {
-  if (!A || kind < 0 || kind > 4 || G < 0 || VPT < 0) return APF_ERR_ARG;
+  if (!A || kind < 0 || kind > 5 || G < 0 || VPT < 0) return APF_ERR_ARG;
   A->pin_kind = kind;
   A->pin_G = G;
   A->pin_VPT = VPT;

@@ -14,32 +14,31 @@
 //     C[m][n] ~ 2^(E_m + F_n - 62) sum_{d=0}^{6} 2^(8 (6 - d)) P_d,
 //     P_d = sum_{s + t = d} sum_k sigma_s(A)[m][k] sigma_t(B)[n][k],
 // dropping the pairs s + t >= 7 (below 2^-56 of the leading term, as the
-// rounding of F).  P_d over a chunk of 32 values of k is an integer below
-// 7 x 32 x 2^14 < 2^22, so the tensor cores' FP32 accumulation is exact in
-// any order.  After each chunk the seven FP32 sums are turned into integers
-// exactly by adding 1.5 x 2^23 (the integer then sits in the low mantissa
-// bits) and accumulated in 32-bit integers (at most 512 chunks per CTA keeps
-// them below 2^31); at the end of the CTA they are folded into two 64-bit
-// integers,  hi = P_0 2^16 + P_1 2^8 + P_2,  lo = P_3 2^24 + P_4 2^16 + P_5 2^8 + P_6,
+// rounding of F).  P_d gains at most (d + 1) x 32 x 2^14 in magnitude per
+// 32-wide chunk of k, so the tensor cores' FP32 accumulation stays exact (every
+// partial sum an integer within 2^24) over floor(32 / (d + 1)) chunks: from 32
+// chunks for d = 0 to 4 for d = 6.  At the end of each such period the FP32 sum
+// is read out, converted to an integer exactly, and added into two 64-bit
+// integers per output element,
+//     hi = P_0 2^16 + P_1 2^8 + P_2,  lo = P_3 2^24 + P_4 2^16 + P_5 2^8 + P_6,
 // so C = 2^(E_m + F_n - 62) (hi 2^32 + lo) is formed once, in FP64.  (FP64
 // arithmetic runs at a tiny fraction of the tensor rate on this part: the
 // carry never touches it.)  Split-K partial sums are added with 64-bit
 // integer atomics, which is exact and independent of the order.
 //
-// Kernel (one CTA per 128 x 32 output tile and K range, 320 threads):
-//   warp 8  producer: per 32-wide k chunk, bulk copies (cp.async.bulk) of the
-//           seven 128 x 32 digit tiles of A and the seven 32 x 32 tiles of B,
-//           stored pre-swizzled (64-byte swizzle) in global memory, into a
-//           three-stage ring;
-//   warp 9  MMA issuer: 28 slice pairs x 2 k steps of tcgen05.mma
-//           (M = 128, N = 32, K = 16, bf16 in, FP32 accumulate) into one of
-//           two sets of seven TMEM accumulators (7 x 32 columns each);
-//   warps 0-7  drain: read the accumulators with tcgen05.ld (warp w owns TMEM
-//           lanes 32 (w mod 4) .. +31, i.e. rows of the tile, and columns
-//           16 (w / 4) .. +15) and accumulate the integers.
-// The stages and accumulator sets are handed over with mbarriers; every wait
-// is bounded in time and a timeout makes all roles stop, let their copies
-// land, free the TMEM and record DEV_BARRIER_TIMEOUT.
+// Kernel (one CTA per 128 x nt output tile, nt <= 64, and K range; 320
+// threads, details at k_oz_umma): a producer warp brings the digit tiles of
+// each chunk into a two-stage ring with bulk copies (cp.async.bulk) of
+// pre-swizzled (64-byte swizzle) digit planes, one mbarrier per digit; an MMA
+// warp issues the 28 digit pairs of a chunk (2 k steps each) as tcgen05.mma
+// (M = 128, N = nt, K = 16, bf16 in, FP32 accumulate) into seven TMEM
+// accumulators of 64 columns, one per diagonal; eight drain warps read an
+// accumulator with tcgen05.ld when its period ends.  The MMA reads A (128 x 16)
+// and B (nt x 16) from shared memory for 2 x 128 x nt x 16 flops: a 64-wide
+// tile reads 40 % fewer operand bytes per flop than a 32-wide one.
+// Every wait is bounded in time and a timeout makes all roles stop, let their
+// copies and MMAs in flight complete, free the TMEM and record
+// DEV_BARRIER_TIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -50,15 +49,20 @@ namespace apf {
 
 constexpr int OZS = 7;        // digits per value
 constexpr int OZ_BM = 128;    // output tile rows (MMA M)
-constexpr int OZ_BN = 32;     // output tile columns (MMA N)
+constexpr int OZ_BN = 64;     // output tile columns (MMA N; the last tile of a range may be narrower)
+constexpr int OZ_NQ = 16;     // granularity of a tile's width (MMA N multiple of 16 for M = 128)
 constexpr int OZ_KC = 32;     // k per chunk (one 64-byte swizzle row of bf16)
-constexpr int OZ_ACC = OZS * OZ_BN;        // TMEM columns of one accumulator set
 constexpr uint32_t OZ_A_SLICE = OZ_BM * OZ_KC * 2;   // 8 KB
-constexpr uint32_t OZ_B_SLICE = OZ_BN * OZ_KC * 2;   // 2 KB
+constexpr uint32_t OZ_B_SLICE = OZ_BN * OZ_KC * 2;   // 4 KB (a narrower tile uses the front)
 constexpr uint32_t OZ_A_STAGE = OZS * OZ_A_SLICE;    // 56 KB
-constexpr uint32_t OZ_B_STAGE = OZS * OZ_B_SLICE;    // 14 KB
-constexpr int OZ_STAGES = 3;                        // operand ring depth
+constexpr uint32_t OZ_B_STAGE = OZS * OZ_B_SLICE;    // 28 KB
+constexpr int OZ_STAGES = 2;                        // operand ring depth
 constexpr size_t OZ_SMEM = 1024 + OZ_STAGES * (size_t)(OZ_A_STAGE + OZ_B_STAGE) + 1024;
+
+// Drain period of diagonal d, in chunks: P_d gains at most (d + 1) x 32 x 2^14
+// = (d + 1) 2^19 in magnitude per chunk, so floor(32 / (d + 1)) chunks keep
+// every partial sum within 2^24, where FP32 holds integers exactly.
+__host__ __device__ constexpr int oz_period(int d) { return 32 / (d + 1); }
 
 // Digit layout in global memory: chunk-major planes S[kc][s][row][32 k], each
 // 64-byte row already in the 64-byte-swizzled order the MMA reads from shared
@@ -350,6 +354,10 @@ __device__ __forceinline__ bool oz_wait(uint64_t* bar, uint32_t parity, uint64_t
   return true;
 }
 
+struct OzTile {
+  int m0, n0, nt, pad;  // first output row and column, width (a multiple of 16, <= 64)
+};
+
 struct OzArgs {
   const __nv_bfloat16* SA;  // digit planes of A (rowsA rows) and B (rowsB rows)
   const __nv_bfloat16* SB;
@@ -357,8 +365,7 @@ struct OzArgs {
   int mode;          // 0: Gram (int64 atomics into H, L); 1: tall product (FP64 out)
   int64_t chunks;    // k chunks of this product (KT / OZ_KC)
   int64_t chunks_per_split;
-  int ntile_n;       // output tiles along n
-  const int2* tiles; // (tile m, tile n) per blockIdx.x
+  const OzTile* tiles;  // per blockIdx.x
   // mode 0: complex Im half of the n range: B rows shifted by half_k chunks, negated past it
   int n_im0;         // first n of the imaginary half (or a large value)
   int64_t half_chunks;
@@ -382,40 +389,58 @@ struct OzArgs {
 
 constexpr int OZ_THREADS = 320;
 constexpr int OZ_DRAIN = 256;       // drain threads (warps 0-7)
-constexpr int OZ_MAX_CHUNKS = 512;  // per CTA: keeps the 32-bit sums below 2^31
 
+// One CTA: a 128 x nt output tile over one range of k chunks.
+//   warp 8 (lane 0)  producer: per chunk and digit s, one bulk copy of the A
+//                    tile (128 rows x 32 k) and one of the B tile (nt rows),
+//                    completing on the barrier of (stage, s), so the MMAs of
+//                    diagonal d start once digits 0..d have landed;
+//   warp 9 (lane 0)  MMA issuer: diagonal d of a chunk is the d + 1 digit
+//                    pairs (s, d - s), two k steps each, accumulated into TMEM
+//                    columns 64 d .. 64 d + nt - 1; the first product of a
+//                    drain period overwrites;
+//   warps 0-7        drain: at the end of each period of diagonal d (and of
+//                    the range) read its accumulator (warp w: TMEM lanes
+//                    32 (w mod 4) .., columns 32 (w / 4) ..), convert the exact
+//                    FP32 integers and add them, shifted by the diagonal's
+//                    weight, into two 64-bit integers per output element:
+//                    hi = P_0 2^16 + P_1 2^8 + P_2, lo = P_3 2^24 + ... + P_6.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 k_oz_umma(OzArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1 KB-aligned operand area (the swizzle atoms need 512-byte alignment)
   const uint32_t base_s = smem_addr(smem_raw);
   unsigned char* smem = smem_raw + ((1024 - (base_s & 1023)) & 1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem);        // [3] bulk copies -> MMA
-  uint64_t* empty = full + OZ_STAGES;                         // [3] MMA -> producer
-  uint64_t* tfull = empty + OZ_STAGES;                        // [2] MMA -> drain
-  uint64_t* tempty = tfull + 2;                               // [2] drain -> MMA
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tempty + 2);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tempty + 3);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);        // [stage][digit] bulk copies -> MMA
+  uint64_t* empty = full + OZ_STAGES * OZS;                   // [stage] MMA -> producer
+  uint64_t* tfull = empty + OZ_STAGES;                        // [d] MMA -> drain
+  uint64_t* tempty = tfull + OZS;                             // [d] drain -> MMA
+  uint64_t* fin = tempty + OZS;                               // MMAs in flight at an abort
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(fin + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  int* issued = const_cast<int*>(abort_flag) + 1;             // chunks the producer issued
+  int* fin_armed = issued + 1;                                // the MMA issuer committed `fin`
   unsigned char* opA = smem + 1024;
   unsigned char* opB = opA + OZ_STAGES * OZ_A_STAGE;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int2 tile = a.tiles[blockIdx.x];
-  const int m0 = tile.x * OZ_BM, n0 = tile.y * OZ_BN;
+  const OzTile tile = a.tiles[blockIdx.x];
+  const int m0 = tile.m0, n0 = tile.n0, nt = tile.nt;
   const int64_t c_begin = (int64_t)blockIdx.y * a.chunks_per_split;
   const int64_t c_end = min(a.chunks, c_begin + a.chunks_per_split);
   const int nch = (int)(c_end > c_begin ? c_end - c_begin : 0);
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < OZ_STAGES; ++i) {
-      mbar_init(full + i, 1);
-      mbar_init(empty + i, 1);
+    for (int i = 0; i < OZ_STAGES * OZS; ++i) mbar_init(full + i, 1);
+    for (int i = 0; i < OZ_STAGES; ++i) mbar_init(empty + i, 1);
+    for (int d = 0; d < OZS; ++d) {
+      mbar_init(tfull + d, 1);
+      mbar_init(tempty + d, OZ_DRAIN);
     }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(tfull + i, 1);
-      mbar_init(tempty + i, OZ_DRAIN);
-    }
+    mbar_init(fin, 1);
     *abort_flag = 0;
+    *issued = 0;
+    *fin_armed = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -429,129 +454,136 @@ k_oz_umma(OzArgs a) {
 
   // the imaginary half of a complex Gram: B rows from the other half of k, negated in the second
   const bool im_tile = a.mode == 0 && n0 >= a.n_im0;
+  const uint32_t b_bytes = (uint32_t)nt * OZ_KC * 2;
 
   if (warp == 8) {
     if (lane == 0) {
       const int nb = im_tile ? n0 - a.n_im0 : n0;
-      for (int c = 0; c < nch; ++c) {
+      int c = 0;
+      for (; c < nch; ++c) {
         const int st = c % OZ_STAGES, use = c / OZ_STAGES;
         if (c >= OZ_STAGES && !oz_wait(empty + st, (uint32_t)((use - 1) & 1), a.limit_ns, abort_flag)) break;
         const int64_t kc = c_begin + c;
         int64_t kb = kc;
         if (im_tile) kb = kc < a.half_chunks ? kc + a.half_chunks : kc - a.half_chunks;
-        mbar_arrive_expect(full + st, OZ_A_STAGE + OZ_B_STAGE);
         for (int sl = 0; sl < OZS; ++sl) {
-          bulk_g2s(opA + st * OZ_A_STAGE + sl * OZ_A_SLICE, a.SA + oz_off(kc, sl, m0, a.rowsA, 0), OZ_A_SLICE, full + st);
-          bulk_g2s(opB + st * OZ_B_STAGE + sl * OZ_B_SLICE, a.SB + oz_off(kb, sl, nb, a.rowsB, 0), OZ_B_SLICE, full + st);
+          uint64_t* bar = full + st * OZS + sl;
+          mbar_arrive_expect(bar, OZ_A_SLICE + b_bytes);
+          bulk_g2s(opA + st * OZ_A_STAGE + sl * OZ_A_SLICE, a.SA + oz_off(kc, sl, m0, a.rowsA, 0), OZ_A_SLICE, bar);
+          bulk_g2s(opB + st * OZ_B_STAGE + sl * OZ_B_SLICE, a.SB + oz_off(kb, sl, nb, a.rowsB, 0), b_bytes, bar);
         }
       }
+      *issued = c;
     }
   } else if (warp == 9) {
     if (lane == 0) {
-      const uint32_t id_pos = umma_idesc(OZ_BM, OZ_BN, false);
-      const uint32_t id_neg = umma_idesc(OZ_BM, OZ_BN, true);
-      for (int c = 0; c < nch; ++c) {
-        const int st = c % OZ_STAGES, b = c & 1;
-        if (!oz_wait(full + st, (uint32_t)((c / OZ_STAGES) & 1), a.limit_ns, abort_flag)) break;
-        if (c >= 2 && !oz_wait(tempty + b, (uint32_t)(((c >> 1) - 1) & 1), a.limit_ns, abort_flag)) break;
-        tc_fence_after();
+      const uint32_t id_pos = umma_idesc(OZ_BM, nt, false);
+      const uint32_t id_neg = umma_idesc(OZ_BM, nt, true);
+      bool any = false;
+      for (int c = 0; c < nch && !*abort_flag; ++c) {
+        const int st = c % OZ_STAGES;
+        const uint32_t ph = (uint32_t)((c / OZ_STAGES) & 1);
         const uint32_t idesc = (im_tile && c_begin + c >= a.half_chunks) ? id_neg : id_pos;
         // descriptors of the stage's first tiles; the other tiles are at fixed
         // offsets (the 14-bit address field holds addr / 16 and never carries)
         const uint64_t ad0 = umma_desc_sw64(smem_addr(opA + st * OZ_A_STAGE));
         const uint64_t bd0 = umma_desc_sw64(smem_addr(opB + st * OZ_B_STAGE));
-        const uint32_t dt0 = tbase + (uint32_t)(b * OZ_ACC);
+        bool ok = true;
 #pragma unroll
         for (int d = 0; d < OZS; ++d) {
+          const int per = oz_period(d);
+          const bool first = c % per == 0;
+          if (!oz_wait(full + st * OZS + d, ph, a.limit_ns, abort_flag)) { ok = false; break; }
+          if (first && c > 0 &&
+              !oz_wait(tempty + d, (uint32_t)((c / per - 1) & 1), a.limit_ns, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t dt = tbase + (uint32_t)(d * OZ_BN);
 #pragma unroll
           for (int s = 0; s <= d; ++s) {
 #pragma unroll
             for (int kk = 0; kk < OZ_KC / 16; ++kk) {
               const uint64_t ad = ad0 + (uint64_t)((s * OZ_A_SLICE + kk * 32) >> 4);
               const uint64_t bd = bd0 + (uint64_t)(((d - s) * OZ_B_SLICE + kk * 32) >> 4);
-              if (s == 0 && kk == 0) umma_bf16_first(dt0 + d * OZ_BN, ad, bd, idesc);
-              else umma_bf16_acc(dt0 + d * OZ_BN, ad, bd, idesc);
+              if (first && s == 0 && kk == 0) umma_bf16_first(dt, ad, bd, idesc);
+              else umma_bf16_acc(dt, ad, bd, idesc);
             }
           }
+          any = true;
+          if ((c + 1) % per == 0 || c == nch - 1) umma_commit(tfull + d);
         }
+        if (!ok) break;
         umma_commit(empty + st);
-        umma_commit(tfull + b);
+      }
+      if (*abort_flag && any) {
+        umma_commit(fin);
+        *fin_armed = 1;
       }
     }
   } else {
-    // drain: thread = row 32 (warp mod 4) + lane of the tile, columns 16 (warp / 4) + 0..15
-    constexpr int HC = OZ_BN / 2;
     const int quarter = warp & 3, half = warp >> 2;
-    int acc[OZS][HC];
+    const int col0 = half * 32;            // first column of this warp within the tile
+    const bool active = col0 < nt;
+    const bool second = nt - col0 > 16;    // its second group of 16 columns is in the tile
+    long long hi[32], lo[32];
 #pragma unroll
-    for (int d = 0; d < OZS; ++d)
-#pragma unroll
-      for (int j = 0; j < HC; ++j) acc[d][j] = 0;
+    for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    // an exact FP32 integer v, |v| < 2^22: the bits of v + 1.5 2^23 are MAGIC + v
-    constexpr float kMagicF = 12582912.0f;
-    constexpr int kMagicI = 0x4B400000;
     bool ok = true;
-    for (int c = 0; c < nch; ++c) {
-      const int b = c & 1;
-      if (!oz_wait(tfull + b, (uint32_t)((c >> 1) & 1), a.limit_ns, abort_flag)) {
-        ok = false;
-        break;
+    for (int c = 0; c < nch && ok; ++c) {
+#pragma unroll
+      for (int d = 0; d < OZS; ++d) {
+        const int per = oz_period(d);
+        if (!((c + 1) % per == 0 || c == nch - 1)) continue;
+        if (!oz_wait(tfull + d, (uint32_t)((c / per) & 1), a.limit_ns, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        // weights: hi = P0 2^16 + P1 2^8 + P2, lo = P3 2^24 + P4 2^16 + P5 2^8 + P6
+        constexpr int kShift[OZS] = {16, 8, 0, 24, 16, 8, 0};
+        uint32_t r[16];
+        if (active) {
+          tmem_ld16(tbase + lane_off + (uint32_t)(d * OZ_BN + col0), r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const long long v = (long long)__float2int_rn(__uint_as_float(r[j])) << kShift[d];
+            if (d < 3) hi[j] += v;
+            else lo[j] += v;
+          }
+          if (second) {
+            tmem_ld16(tbase + lane_off + (uint32_t)(d * OZ_BN + col0 + 16), r);
+            tmem_wait_ld();
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(tempty + d);
+        if (active && second) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const long long v = (long long)__float2int_rn(__uint_as_float(r[j])) << kShift[d];
+            if (d < 3) hi[16 + j] += v;
+            else lo[16 + j] += v;
+          }
+        }
       }
-      tc_fence_after();
-      // two diagonals (16 columns each) per wait: the 112 sums stay in registers
-#pragma unroll
-      for (int d0 = 0; d0 < OZS; d0 += 2) {
-        uint32_t r0[HC], r1[HC];
-        tmem_ld16(tbase + lane_off + (uint32_t)(b * OZ_ACC + d0 * OZ_BN + half * HC), r0);
-        if (d0 + 1 < OZS) tmem_ld16(tbase + lane_off + (uint32_t)(b * OZ_ACC + (d0 + 1) * OZ_BN + half * HC), r1);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < HC; ++j)
-          acc[d0][j] += __float_as_int(__fadd_rn(__uint_as_float(r0[j]), kMagicF)) - kMagicI;
-        if (d0 + 1 < OZS)
-#pragma unroll
-          for (int j = 0; j < HC; ++j)
-            acc[d0 + 1][j] += __float_as_int(__fadd_rn(__uint_as_float(r1[j]), kMagicF)) - kMagicI;
-      }
-      tc_fence_before();
-      mbar_arrive(tempty + b);
     }
-    if (ok && !*abort_flag) {
-      // park the sums in the (now idle) operand area: the fold below then
-      // needs few registers.  The last tfull wait means every MMA, hence every
-      // read of the operand area and every TMA write into it, has completed.
-      int* sacc = reinterpret_cast<int*>(opA) + threadIdx.x * (OZS * HC + 1);
-#pragma unroll
-      for (int d = 0; d < OZS; ++d)
-#pragma unroll
-        for (int j = 0; j < HC; ++j) sacc[d * HC + j] = acc[d][j];
+    if (ok && !*abort_flag && active) {
       const int m = m0 + quarter * 32 + lane;
-      const int nb0 = n0 + half * HC;
-      auto fold = [&](int j, long long& hi, long long& lo) {
-        hi = ((long long)sacc[0 * HC + j] << 16) + ((long long)sacc[1 * HC + j] << 8) + sacc[2 * HC + j];
-        lo = ((long long)sacc[3 * HC + j] << 24) + ((long long)sacc[4 * HC + j] << 16) +
-             ((long long)sacc[5 * HC + j] << 8) + sacc[6 * HC + j];
-      };
+      const int cend = min(nt - col0, 32);
       if (a.mode == 0) {
-#pragma unroll 1
-        for (int j = 0; j < HC; ++j) {
-          long long hi, lo;
-          fold(j, hi, lo);
-          const int64_t o = (int64_t)m * a.NP + nb0 + j;
-          if (hi) atomicAdd(a.H + o, (unsigned long long)hi);
-          if (lo) atomicAdd(a.L + o, (unsigned long long)lo);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (j >= cend) break;
+          const int64_t o = (int64_t)m * a.NP + n0 + col0 + j;
+          if (hi[j]) atomicAdd(a.H + o, (unsigned long long)hi[j]);
+          if (lo[j]) atomicAdd(a.L + o, (unsigned long long)lo[j]);
         }
       } else if (m < a.nrows) {
         const int em = a.ea[m];
-#pragma unroll 1
-        for (int j = 0; j < HC; ++j) {
-          const int col = nb0 + j;
-          if (col >= a.ncols) continue;
-          long long hi, lo;
-          fold(j, hi, lo);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + col0 + j;
+          if (j >= cend || col >= a.ncols) break;
           const int sc = em + a.fb[col] - 62;
-          const double v = oz_scale((double)hi, sc + 32) + oz_scale((double)lo, sc);
+          const double v = oz_scale((double)hi[j], sc + 32) + oz_scale((double)lo[j], sc);
           int64_t oz, oz0;
           if (a.cplx) {
             const int jc = col % a.pb, part = col / a.pb;
@@ -571,15 +603,17 @@ k_oz_umma(OzArgs a) {
   __syncthreads();
   if (*abort_flag) {
     if (threadIdx.x == 0) atomicCAS(a.err, 0, DEV_BARRIER_TIMEOUT);
-    // the last stages' TMA copies and MMAs complete by themselves; wait for
-    // their barriers (bounded) before the shared memory and TMEM go away
-    if (threadIdx.x == 0) {
-      volatile int dummy = 0;
-      for (int c = (nch > OZ_STAGES ? nch - OZ_STAGES : 0); c < nch; ++c)
-        oz_wait(full + c % OZ_STAGES, (uint32_t)((c / OZ_STAGES) & 1), 1000000000ull, &dummy);
-      for (int c = (nch > 2 ? nch - 2 : 0); c < nch; ++c)
-        oz_wait(tfull + (c & 1), (uint32_t)((c >> 1) & 1), 1000000000ull, &dummy);
+    volatile int dummy = 0;
+    if (warp == 8 && lane == 0) {
+      // the last chunks' bulk copies complete by themselves: wait for them
+      // (bounded) before the shared memory goes away
+      const int n_is = *issued;
+      for (int c = (n_is > OZ_STAGES ? n_is - OZ_STAGES : 0); c < n_is; ++c)
+        for (int sl = 0; sl < OZS; ++sl)
+          oz_wait(full + (c % OZ_STAGES) * OZS + sl, (uint32_t)((c / OZ_STAGES) & 1), 1000000000ull, &dummy);
     }
+    if (warp == 9 && lane == 0 && *fin_armed)
+      oz_wait(fin, 0u, 1000000000ull, &dummy);  // every MMA issued has completed
     __syncthreads();
   }
   tc_fence_after();
@@ -587,8 +621,14 @@ k_oz_umma(OzArgs a) {
 }
 
 // hi/lo sums of the Gram -> G (FP64), mirroring the tiles below the diagonal
+// last column of the output tile that holds column j of a range of pbP columns
+__host__ __device__ inline int oz_tile_end(int j, int pbP) {
+  const int b0 = (j / OZ_BN) * OZ_BN;
+  return (b0 + OZ_BN < pbP ? b0 + OZ_BN : pbP) - 1;
+}
+
 template <class T>
-__global__ void k_oz_gram_finish(int pa, int pb, int NP, int n_im0, bool hermitian,
+__global__ void k_oz_gram_finish(int pa, int pb, int pbP, int NP, int n_im0, bool hermitian,
                                  const unsigned long long* __restrict__ H, const unsigned long long* __restrict__ L,
                                  const int* __restrict__ ea, const int* __restrict__ eb, T* __restrict__ G,
                                  int64_t ldg) {
@@ -596,7 +636,7 @@ __global__ void k_oz_gram_finish(int pa, int pb, int NP, int n_im0, bool hermiti
   if (idx >= (int64_t)pa * pb) return;
   const int i = (int)(idx / pb), j = (int)(idx % pb);
   // computed tiles: (tile m, tile n) with n range reaching the m range's start
-  const bool have = !hermitian || (j / OZ_BN) * OZ_BN + OZ_BN - 1 >= (i / OZ_BM) * OZ_BM;
+  const bool have = !hermitian || oz_tile_end(j, pbP) >= (i / OZ_BM) * OZ_BM;
   const int si = have ? i : j, sj = have ? j : i;
   auto val = [&](int col) {
     const int64_t o = (int64_t)si * NP + col;
@@ -630,9 +670,29 @@ static void launch_oz(apf_ctx* ctx, OzArgs& a, int ntiles, int nsplit) {
   allow_large_smem_bytes<k_oz_umma>(ctx->device, (int)OZ_SMEM);
   a.err = ctx->d_err;
   a.limit_ns = filter_wait_ns(ctx);
-  APF_REQUIRE(a.chunks_per_split <= OZ_MAX_CHUNKS, APF_ERR_ARG);
   k_oz_umma<<<dim3((unsigned)ntiles, (unsigned)nsplit), OZ_THREADS, OZ_SMEM, ctx->stream>>>(a);
   count_launch(ctx);
+}
+
+// Output tiles of width <= OZ_BN (multiples of OZ_NQ) over columns [c0, c0 + w).
+static void push_tiles(std::vector<OzTile>& t, int m0, int c0, int w) {
+  for (int b = 0; b < w; b += OZ_BN) t.push_back(OzTile{m0, c0 + b, std::min(OZ_BN, w - b), 0});
+}
+
+// K splits per tile: one CTA per SM at a time, so pick the split count whose
+// grid fills whole waves best (one to four waves), keeping >= 8 chunks a CTA.
+static int64_t pick_splits(int ntiles, int64_t chunks, int num_sms) {
+  const int64_t cap = std::max<int64_t>(1, chunks / 8);
+  if (ntiles >= num_sms) return 1;
+  int64_t best = 1;
+  double best_eff = -1.0;
+  for (int w = 1; w <= 4; ++w) {
+    const int64_t ns = std::min<int64_t>(cap, std::max<int64_t>(1, (int64_t)w * num_sms / ntiles));
+    const int64_t total = ns * ntiles;
+    const double eff = (double)total / (double)(((total + num_sms - 1) / num_sms) * num_sms);
+    if (eff > best_eff + 1e-9) { best_eff = eff; best = ns; }
+  }
+  return best;
 }
 
 template <class T>
@@ -645,7 +705,7 @@ void gram_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_
   const int64_t nK = round_up(n, OZ_KC), KT = C * nK;
   // exactness of the carry: at most 2^16 chunks of k in all
   if (KT / OZ_KC > 65536) { gram<T>(ctx, n, pa, pb, X, ldx, Y, ldy, G, ldg, hermitian); return; }
-  const int paP = (int)round_up(pa, OZ_BM), pbP = (int)round_up(pb, OZ_BN);
+  const int paP = (int)round_up(pa, OZ_BM), pbP = (int)round_up(pb, OZ_NQ);
   const int NP = C * pbP;  // output columns: [re | im]
   const bool same = (X == Y && ldx == ldy && pa == pb);
   const int pyP = same ? paP : pbP;  // rows of Y's slice array
@@ -654,19 +714,22 @@ void gram_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_
   const int64_t rows_per = (n + nb - 1) / nb;
   const size_t sx = (size_t)OZS * paP * KT * 2, sy = same ? 0 : (size_t)OZS * pyP * KT * 2;
   const size_t hl = (size_t)paP * NP * 8;
-  const int ntm = paP / OZ_BM, ntn = NP / OZ_BN;
-  std::vector<int2> tiles;
+  const int ntm = paP / OZ_BM;
+  std::vector<OzTile> tiles;
   for (int tm = 0; tm < ntm; ++tm)
-    for (int tn = 0; tn < ntn; ++tn) {
-      const int b0 = (tn * OZ_BN) % pbP;
-      if (hermitian && b0 + OZ_BN - 1 < tm * OZ_BM) continue;
-      if (b0 >= pb) continue;  // padding columns only
-      tiles.push_back(make_int2(tm, tn));
+    for (int part = 0; part < C; ++part) {
+      std::vector<OzTile> row;
+      push_tiles(row, tm * OZ_BM, 0, pbP);
+      for (const OzTile& t : row) {
+        // below the diagonal of a Hermitian Gram: mirrored by the finish kernel
+        if (hermitian && oz_tile_end(t.n0, pbP) < tm * OZ_BM) continue;
+        tiles.push_back(OzTile{t.m0, t.n0 + part * pbP, t.nt, 0});
+      }
     }
   size_t off = 0;
   auto take = [&](size_t b) { const size_t o = off; off = round_up((int64_t)(off + b), 1024); return o; };
   const size_t o_sx = take(sx), o_sy = take(sy), o_ex = take((size_t)paP * 4), o_ey = take((size_t)pyP * 4);
-  const size_t o_h = take(hl), o_l = take(hl), o_t = take(tiles.size() * sizeof(int2));
+  const size_t o_h = take(hl), o_l = take(hl), o_t = take(tiles.size() * sizeof(OzTile));
   const size_t o_part = take((size_t)nb * std::max(pa, pb) * 8);
   unsigned char* ws = static_cast<unsigned char*>(workspace(ctx, off));
   auto* SX = reinterpret_cast<__nv_bfloat16*>(ws + o_sx);
@@ -675,16 +738,17 @@ void gram_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_
   int* ey = same ? ex : reinterpret_cast<int*>(ws + o_ey);
   auto* H = reinterpret_cast<unsigned long long*>(ws + o_h);
   auto* L = reinterpret_cast<unsigned long long*>(ws + o_l);
-  int2* dtiles = reinterpret_cast<int2*>(ws + o_t);
+  OzTile* dtiles = reinterpret_cast<OzTile*>(ws + o_t);
   double* part = reinterpret_cast<double*>(ws + o_part);
-  APF_CUDA(cudaMemcpyAsync(dtiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
+  APF_CUDA(cudaMemcpyAsync(dtiles, tiles.data(), tiles.size() * sizeof(OzTile), cudaMemcpyHostToDevice,
+                           ctx->stream));
   APF_CUDA(cudaMemsetAsync(H, 0, 2 * hl + (o_l - o_h - hl), ctx->stream));
 
   auto slice = [&](const T* M, int64_t ld, int64_t p, int pP, int* e, __nv_bfloat16* S) {
     k_ozt_colmax<T><<<dim3((unsigned)((p + 127) / 128), (unsigned)nb), 128, 0, ctx->stream>>>(n, (int)p, M, ld,
                                                                                            rows_per, part);
     k_ozt_colexp<<<(unsigned)((pP + 127) / 128), 128, 0, ctx->stream>>>((int)p, (int)nb, part, e, pP);
-    k_ozt_split_cols<T, C><<<dim3((unsigned)(nK / 32), (unsigned)(pP / 32)), 256, 0, ctx->stream>>>(
+    k_ozt_split_cols<T, C><<<dim3((unsigned)(nK / 32), (unsigned)((pP + 31) / 32)), 256, 0, ctx->stream>>>(
         n, (int)p, M, ld, e, nK, KT, pP, S);
     count_launch(ctx, 3);
   };
@@ -705,14 +769,12 @@ void gram_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, int64_
   a.L = L;
   a.NP = NP;
   const int ntiles = (int)tiles.size();
-  int64_t nsplit = (2LL * ctx->num_sms + ntiles - 1) / ntiles;
-  nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, a.chunks / 8 > 0 ? a.chunks / 8 : 1));
-  nsplit = std::max<int64_t>(nsplit, (a.chunks + OZ_MAX_CHUNKS - 1) / OZ_MAX_CHUNKS);
+  int64_t nsplit = pick_splits(ntiles, a.chunks, ctx->num_sms);
   a.chunks_per_split = (a.chunks + nsplit - 1) / nsplit;
   nsplit = (a.chunks + a.chunks_per_split - 1) / a.chunks_per_split;
   launch_oz(ctx, a, ntiles, (int)nsplit);
   k_oz_gram_finish<T><<<(unsigned)((pa * pb + 255) / 256), 256, 0, ctx->stream>>>(
-      (int)pa, (int)pb, NP, C == 2 ? pbP : 0, hermitian, H, L, ex, ey, G, ldg);
+      (int)pa, (int)pb, pbP, NP, C == 2 ? pbP : 0, hermitian, H, L, ex, ey, G, ldg);
   count_launch(ctx);
 }
 template void gram_tc<double>(apf_ctx*, int64_t, int64_t, int64_t, const double*, int64_t, const double*, int64_t,
@@ -728,23 +790,23 @@ void gemm_tall_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, i
   APF_REQUIRE(pa >= 1 && pa <= APF_MAX_P && pb <= APF_MAX_P, APF_ERR_ARG);
   const int64_t KT = round_up(C * pa, OZ_KC);
   const int64_t nP = round_up(n, OZ_BM);
-  const int NT = (int)round_up(C * pb, OZ_BN);
+  const int NT = (int)round_up(C * pb, OZ_NQ);
   const size_t sa = (size_t)OZS * nP * KT * 2, sb = (size_t)OZS * NT * KT * 2;
-  const int ntm = (int)(nP / OZ_BM), ntn = NT / OZ_BN;
+  const int ntm = (int)(nP / OZ_BM);
+  std::vector<OzTile> tiles;
+  for (int tm = 0; tm < ntm; ++tm) push_tiles(tiles, tm * OZ_BM, 0, NT);
   size_t off = 0;
   auto take = [&](size_t b) { const size_t o = off; off = round_up((int64_t)(off + b), 1024); return o; };
   const size_t o_sa = take(sa), o_sb = take(sb), o_ea = take((size_t)nP * 4), o_fb = take((size_t)NT * 4);
-  const size_t o_t = take((size_t)ntm * ntn * sizeof(int2));
+  const size_t o_t = take(tiles.size() * sizeof(OzTile));
   unsigned char* ws = static_cast<unsigned char*>(workspace(ctx, off));
   auto* SA = reinterpret_cast<__nv_bfloat16*>(ws + o_sa);
   auto* SB = reinterpret_cast<__nv_bfloat16*>(ws + o_sb);
   int* ea = reinterpret_cast<int*>(ws + o_ea);
   int* fb = reinterpret_cast<int*>(ws + o_fb);
-  int2* dtiles = reinterpret_cast<int2*>(ws + o_t);
-  std::vector<int2> tiles((size_t)ntm * ntn);
-  for (int tm = 0; tm < ntm; ++tm)
-    for (int tn = 0; tn < ntn; ++tn) tiles[(size_t)tm * ntn + tn] = make_int2(tm, tn);
-  APF_CUDA(cudaMemcpyAsync(dtiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
+  OzTile* dtiles = reinterpret_cast<OzTile*>(ws + o_t);
+  APF_CUDA(cudaMemcpyAsync(dtiles, tiles.data(), tiles.size() * sizeof(OzTile), cudaMemcpyHostToDevice,
+                           ctx->stream));
   k_ozt_rowexp<T, C><<<(unsigned)((nP + 7) / 8), 256, 0, ctx->stream>>>(n, (int)pa, X, ldx, nP, ea);
   k_ozt_split_rows<T, C><<<(unsigned)((nP * KT + 255) / 256), 256, 0, ctx->stream>>>(n, (int)pa, X, ldx, ea, nP, KT,
                                                                                      SA);
@@ -772,7 +834,8 @@ void gemm_tall_tc(apf_ctx* ctx, int64_t n, int64_t pa, int64_t pb, const T* X, i
   a.ldz0 = Z0 ? ldz0 : ldz;
   a.alpha = alpha;
   a.beta = Z0 ? beta : 0.0;
-  launch_oz(ctx, a, ntm * ntn, 1);
+  APF_REQUIRE(tiles.size() <= (size_t)INT32_MAX, APF_ERR_ARG);
+  launch_oz(ctx, a, (int)tiles.size(), 1);
 }
 template void gemm_tall_tc<double>(apf_ctx*, int64_t, int64_t, int64_t, const double*, int64_t, const double*,
                                    int64_t, double*, int64_t, double, double, const double*, int64_t);

@@ -54,9 +54,9 @@ void clenshaw_step_sell_ct(apf_ctx* ctx, int G, int VPT, int64_t n, const int64_
                            const T* Y, int64_t ld, int64_t ncols,
                            const typename ScalarTraits<T>::Real* coef_col,
                            typename ScalarTraits<T>::Real coef_scalar,
-                           typename ScalarTraits<T>::Real alpha, T* Out) {
+                           typename ScalarTraits<T>::Real alpha, T* Out, int halo) {
   clenshaw_sell_ct_launch<T, TA>(ctx, G, VPT, n, chunk_ptr, scol, sval, lmax, W, Vin, Y, ld, ncols, coef_col,
-                                 coef_scalar, alpha, Out);
+                                 coef_scalar, alpha, Out, halo);
 }
 
 template <class TA>
@@ -87,7 +87,7 @@ void sell_gather_values(apf_ctx* ctx, int64_t slots, const int32_t* src, const T
                                          int64_t, const float*, float, float, T*);                    \
   template void clenshaw_step_sell_ct<T, T>(apf_ctx*, int, int, int64_t, const int64_t*, const int32_t*, \
                                             const T*, int, const T*, const T*, const T*, int64_t,        \
-                                            int64_t, const float*, float, float, T*);                    \
+                                            int64_t, const float*, float, float, T*, int);               \
   template void sell_gather_values<T>(apf_ctx*, int64_t, const int32_t*, const T*, T*);              \
   template void clenshaw_sell_pair<T, T>(apf_ctx*, int, int, int64_t, const int64_t*, const int32_t*, \
                                          const T*, int, int64_t, T*, T*, const T*, const T*, int64_t, \

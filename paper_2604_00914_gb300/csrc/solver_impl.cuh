@@ -21,12 +21,20 @@
 namespace apf {
 
 // ---- Alg. 2: the Clenshaw recurrence over device buffers -------------------------------
+template <class S>
+struct Stepper;
+
 // Counters of the SpMM launches of one filter application.
 struct FilterCount {
   int64_t launches = 0;   // kernel launches
   int64_t steps = 0;      // Clenshaw steps (a two-step launch counts 2)
   double bytes = 0.0;     // algorithmic bytes of the launched kernels
   double step_bytes = 0.0;  // algorithmic bytes of the same steps run one per launch
+  int kind = -1, G = 0, VPT = 0;  // FP32 step kernel of the first (widest) application
+  template <class S>
+  void note(const Stepper<S>& st) {
+    if (kind < 0) { kind = st.kind == 0 ? 3 : st.kind; G = st.G; VPT = st.VPT; }  // internal 0 = CSR
+  }
 };
 
 static double step_bytes(int64_t n, int64_t nnz, int64_t p, size_t sval, size_t sblk, bool vin,
@@ -57,7 +65,8 @@ struct Stepper {
   size_t seg_bytes = 0;
   int64_t ld = 0;
   // kind 1: SELL, one step per launch; 2: SELL, two steps per launch; 4: SELL,
-  // one column tile of G x VPT vectors per CTA (any width); 0: CSR
+  // one column tile of G x VPT vectors per CTA (any width); 5: as 4, with the
+  // matrix's near rows of W staged in shared memory; 0: CSR
   int kind = 0, G = 0, VPT = 0;
   unsigned* seg_count = nullptr;  // pair-pass counters (kind 2)
   unsigned* pass = nullptr;       // passes made with seg_count
@@ -79,10 +88,11 @@ struct Stepper {
   }
   void operator()(const S* W, const S* Vin, const S* Y, int64_t ncols, const Real* coef_col,
                   Real coef_scalar, Real alpha, S* Out) const {
-    if (kind == 4) {
+    if (kind == 4 || kind == 5) {
       if constexpr (sizeof(Real) == 4)
         clenshaw_step_sell_ct<S, S>(ctx, G, VPT, A->n, A->sell_chunk_ptr, A->sell_col, sell_vals, A->sell_lmax, W,
-                                    Vin, Y, ld, ncols, coef_col, coef_scalar, alpha, Out);
+                                    Vin, Y, ld, ncols, coef_col, coef_scalar, alpha, Out,
+                                    kind == 5 ? A->sell_halo : 0);
     } else if (kind >= 1) {
       // the two-step form keeps its blocks in the permuted row order: its
       // single steps (the last one or two) must use the permuted copy too
@@ -111,10 +121,10 @@ constexpr int kNumSellCtShapes = (int)(sizeof(kSellCtShapes) / sizeof(kSellCtSha
 // a column-tiled shape applies when its shared memory fits and the grid's
 // tile dimension stays within range
 template <class S>
-static bool sell_ct_fits(const Stepper<S>& st, int G, int VPT, int nvec) {
+static bool sell_ct_fits(const Stepper<S>& st, int G, int VPT, int nvec, int halo = 0) {
   const int TV = G * VPT;
-  return sell_ct_smem_bytes(256 / G, TV, st.A->sell_lmax, sizeof(S)) <= 160 * 1024 &&
-         (nvec + TV - 1) / TV <= 65535 && st.A->n <= INT32_MAX;
+  return sell_ct_smem_bytes(256 / G, TV, st.A->sell_lmax, sizeof(S), halo) <= 160 * 1024 &&
+         256 / G + 2 * halo <= 256 && (nvec + TV - 1) / TV <= 65535 && st.A->n <= INT32_MAX;
 }
 
 // idle fraction of the vector slots of the column tiles covering nvec vectors
@@ -140,16 +150,18 @@ template <class S>
 static void pinned_shape(Stepper<S>& st, int nvec) {
   const apf_matrix* A = st.A;
   int kind = A->pin_kind == 3 ? 0 : A->pin_kind;
-  if (kind == 4) {
+  if (kind == 5 && A->sell_halo == 0) kind = 4;
+  if (kind == 4 || kind == 5) {
     if (A->sell_ok) {
+      const int halo = kind == 5 ? A->sell_halo : 0;
       int bg = 0, bv = 0;
       for (int i = 0; i < kNumSellCtShapes; ++i) {
         const int g = kSellCtShapes[i].G, v = kSellCtShapes[i].VPT;
-        if (!sell_ct_fits(st, g, v, nvec)) continue;
+        if (!sell_ct_fits(st, g, v, nvec, halo)) continue;
         if (g == A->pin_G && v == A->pin_VPT) { bg = g; bv = v; break; }
         if (bg == 0 || ct_idle(g, v, nvec) < ct_idle(bg, bv, nvec) - 1e-12) { bg = g; bv = v; }
       }
-      if (bg) { st.kind = 4; st.G = bg; st.VPT = bv; return; }
+      if (bg) { st.kind = kind; st.G = bg; st.VPT = bv; return; }
     }
     kind = 1;
   }
@@ -187,12 +199,13 @@ static void pinned_shape(Stepper<S>& st, int nvec) {
   st.VPT = bv;
 }
 
-// Autotuner: time each candidate shape on the live buffers (one warm-up and
-// three timed launches) and keep the fastest per (element size, ld, width) in
-// the matrix.  All shapes do the same arithmetic in the same order, so the
-// choice changes the time, never the result.
+// Autotuner: time each candidate shape on the live buffers (one warm-up pass
+// and four timed steps each; W, Y and an in-place V = output distinct, as in
+// the recurrence) and keep the fastest per (element size, ld, width) in the
+// matrix.  All shapes do the same arithmetic in the same order, so the choice
+// changes the time, never the result.
 template <class S>
-static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, const S* Yb, S* Ob) {
+static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Yb, S* Ob) {
   using Real = typename ScalarTraits<S>::Real;
   constexpr int E = ScalarTraits<S>::per16;
   st.kind = 0;
@@ -254,6 +267,8 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
       if (!sell_ct_fits(st, g, v, nvec)) continue;
       if (ct_idle(g, v, nvec) > 0.5 && i != least) continue;
       cands.push_back({4, g, v});
+      // and with the near rows of W in shared memory, where the matrix has them
+      if (A->sell_halo > 0 && sell_ct_fits(st, g, v, nvec, A->sell_halo)) cands.push_back({5, g, v});
     }
   }
   APF_REQUIRE(!cands.empty(), APF_ERR_ARG);
@@ -275,17 +290,20 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Vb, co
     t.kind = c.kind;
     t.G = c.G;
     t.VPT = c.VPT;
-    // time per Clenshaw step: 4 single steps, or 2 two-step passes
+    // time per Clenshaw step: 4 single steps, or 2 two-step passes, on the
+    // buffers the way the recurrence uses them: W, Y and V distinct, the
+    // output over V (b_j replaces b_{j+2})
     auto run = [&]() {
       if (t.pairs()) {
         APF_CUDA(cudaMemsetAsync(t.seg_count, 0, st.seg_bytes, st.ctx->stream));
         *t.pass = 0;
-        t.pair(Ob, const_cast<S*>(Vb), Wb, Yb, p, nullptr, (Real)0.5, nullptr, (Real)0.25);
-        t.pair(Ob, const_cast<S*>(Vb), Vb, Yb, p, nullptr, (Real)0.5, nullptr, (Real)0.25);
+        t.pair(const_cast<S*>(Wb), Ob, Ob, Yb, p, nullptr, (Real)0.5, nullptr, (Real)0.25);
+        t.pair(const_cast<S*>(Wb), Ob, Ob, Yb, p, nullptr, (Real)0.5, nullptr, (Real)0.25);
       } else {
-        for (int r = 0; r < 4; ++r) t(Wb, Vb, Yb, p, nullptr, (Real)0.5, (Real)2, Ob);
+        for (int r = 0; r < 4; ++r) t(Wb, Ob, Yb, p, nullptr, (Real)0.5, (Real)2, Ob);
       }
     };
+    if (&c == &cands[0]) run();  // the GPU's clocks settle before the first timing
     run();
     APF_CUDA(cudaEventRecord(e0, st.ctx->stream));
     run();
@@ -673,7 +691,7 @@ struct FilterState {
     s.seg_count = A->sell_ok ? segs.as<unsigned>() : nullptr;
     s.seg_bytes = A->sell_ok ? seg_bytes() : 0;
     s.pass = &pass;
-    tune_stepper<TL>(s, p, Y32.as<TL>(), B2.as<TL>(), Y32.as<TL>(), B1.as<TL>());
+    tune_stepper<TL>(s, p, B1.as<TL>(), Y32.as<TL>(), B2.as<TL>());
     if (s.pairs()) {  // fresh counters for this application's passes
       APF_CUDA(cudaMemsetAsync(segs.p, 0, seg_bytes(), ctx->stream));
       pass = 0;
@@ -697,6 +715,7 @@ struct FilterState {
       return;
     }
     const Stepper<TL> st = stepper32(p);
+    if (fc) fc->note(st);
     if (precision == APF_FILTER_F32_DEFECT && AV != nullptr && lam != nullptr) {
       // R_hat = l1 (A V - V diag(lam)) in FP32, in the recurrence's row order;
       // the norms are not needed here
@@ -751,6 +770,7 @@ struct FilterState {
       return;
     }
     const Stepper<TL> st = stepper32(p);
+    if (fc) fc->note(st);
     APF_CUDA(cudaMemsetAsync(B1.p, 0, B1.bytes, ctx->stream));
     APF_CUDA(cudaMemsetAsync(B2.p, 0, B2.bytes, ctx->stream));
     DBuf Ff((size_t)(K + 1) * ld * sizeof(float), ctx->stream, false);
@@ -1190,6 +1210,9 @@ static void finish_stats(apf_ctx* ctx, const std::vector<IterEv>& iev, const Fil
   st->filter_steps = fc.steps;
   st->filter_bytes = fc.bytes;
   st->filter_step_bytes = fc.step_bytes;
+  st->filter_kind = fc.kind;
+  st->filter_g = fc.G;
+  st->filter_vpt = fc.VPT;
 }
 
 struct Bounds {

@@ -20,6 +20,14 @@
 // the W rows are gathered into registers meanwhile.  Each row sums its entries
 // in CSR order and the epilogue is the same fused operation as in the other
 // kernels, so every variant gives the same bits.  Waits are bounded in time.
+//
+// Near rows (halo H > 0): the rows of a stencil's own grid line sit within a
+// few rows of the diagonal, so the R rows of a CTA share them.  With a halo the
+// CTA also copies rows r0 - H .. r0 + R + H - 1 of W's tile into shared memory
+// (one more 2-D TMA copy; rows outside the matrix read as zero) and reads the
+// entries whose column falls there from shared memory instead of L2: for the
+// 25-point stencil of a 3D eighth-order Laplacian, 9 of the 25 gathered rows.
+// The values read are the same, so the bits are too.
 #pragma once
 #include <cuda.h>
 
@@ -36,9 +44,10 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// shared-memory bytes of one CTA: barrier, Y and Vin tiles, structure
-inline size_t sell_ct_smem_bytes(int R, int TV, int lmax, size_t sTA) {
+// shared-memory bytes of one CTA: barrier, Y and Vin tiles, near rows of W, structure
+inline size_t sell_ct_smem_bytes(int R, int TV, int lmax, size_t sTA, int halo = 0) {
   size_t b = 128 + 2 * (size_t)R * TV * 16;
+  if (halo > 0) b += (size_t)(R + 2 * halo) * TV * 16;
   b += (size_t)R * lmax * 4;
   b = (b + 15) / 16 * 16;
   b += (size_t)R * lmax * sTA;
@@ -50,7 +59,8 @@ template <class T, class TA, int G, int VPT>
 __global__ void __launch_bounds__(256, (VPT <= 2 ? 4 : 3))
 k_clenshaw_sell_ct(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32_t* __restrict__ scol,
                    const TA* __restrict__ sval, int lmax, const T* __restrict__ W,
-                   const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmY, int has_v,
+                   const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmY,
+                   const __grid_constant__ CUtensorMap tmW, int halo, int has_v,
                    int has_y, int64_t ld, int nvec, const typename ScalarTraits<T>::Real* __restrict__ coef_col,
                    typename ScalarTraits<T>::Real coef_scalar, typename ScalarTraits<T>::Real alpha,
                    T* __restrict__ Out, int* err, uint64_t limit_ns) {
@@ -62,7 +72,9 @@ k_clenshaw_sell_ct(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   uint4* Ys = reinterpret_cast<uint4*>(smem + 128);
   uint4* Vs = Ys + R * TV;
-  int32_t* cols = reinterpret_cast<int32_t*>(Vs + R * TV);
+  uint4* Ws = Vs + R * TV;                 // near rows of W (halo > 0)
+  const int wn = halo > 0 ? R + 2 * halo : 0;
+  int32_t* cols = reinterpret_cast<int32_t*>(Ws + wn * TV);
   size_t voff = (size_t)((unsigned char*)(cols + R * lmax) - smem);
   voff = (voff + 15) / 16 * 16;
   TA* vals = reinterpret_cast<TA*>(smem + voff);
@@ -78,11 +90,12 @@ k_clenshaw_sell_ct(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32
     mbar_init(bar, 1);
     fence_mbar_init();
     const uint32_t tile = (uint32_t)(R * TV * 16);
-    const uint32_t yv = (has_y ? tile : 0u) + (has_v ? tile : 0u);
+    const uint32_t yv = (has_y ? tile : 0u) + (has_v ? tile : 0u) + (uint32_t)(wn * TV * 16);
     if (yv) mbar_expect_tx(bar, yv);
     // x in 4-byte units (the maps describe the block as floats)
     if (has_y) tma_load_2d(Ys, &tmY, v0 * 4, (int)r0, bar);
     if (has_v) tma_load_2d(Vs, &tmV, v0 * 4, (int)r0, bar);
+    if (wn) tma_load_2d(Ws, &tmW, v0 * 4, (int)r0 - halo, bar);
     for (int c = 0; c <= nch; ++c) cps[c] = chunk_ptr[c0 + c];
     const int64_t e0 = cps[0], e1 = cps[nch];
     const uint32_t nc = (uint32_t)((e1 - e0) * 4), nv = (uint32_t)((e1 - e0) * sizeof(TA));
@@ -113,18 +126,21 @@ k_clenshaw_sell_ct(int64_t n, const int64_t* __restrict__ chunk_ptr, const int32
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[q][e] = szero<T>();
 
+  const int wlo = (int)r0 - halo;
 #pragma unroll 4
   for (int t = 0; t < len; ++t) {
     const int64_t s = base + (int64_t)t * SELL_C + rr;
     const int col = cols[s];
     const TA v = vals[s];
-    const uint4* wrow = reinterpret_cast<const uint4*>(W + (int64_t)col * ld) + v0;
+    const unsigned rel = (unsigned)(col - wlo);
+    const bool near = rel < (unsigned)wn;
+    const uint4* wrow = near ? Ws + (int64_t)rel * TV : reinterpret_cast<const uint4*>(W + (int64_t)col * ld) + v0;
 #pragma unroll
     for (int q = 0; q < VPT; ++q) {
       const int vl = lane + q * G;
       if (v0 + vl < nvec) {
         Pack16<T> w;
-        w.u = __ldg(wrow + vl);
+        w.u = near ? wrow[vl] : __ldg(wrow + vl);
 #pragma unroll
         for (int e = 0; e < E; ++e) madd(acc[q][e], v, w.t[e]);
       }
@@ -158,20 +174,26 @@ void clenshaw_sell_ct_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const int6
                              const T* Y, int64_t ld, int64_t ncols,
                              const typename ScalarTraits<T>::Real* coef_col,
                              typename ScalarTraits<T>::Real coef_scalar,
-                             typename ScalarTraits<T>::Real alpha, T* Out) {
+                             typename ScalarTraits<T>::Real alpha, T* Out, int halo = 0) {
   constexpr int E = ScalarTraits<T>::per16;
   APF_REQUIRE(ld % E == 0 && W != Out, APF_ERR_ARG);
   if (n == 0 || ncols == 0) return;
   const int nvec = (int)((ncols + E - 1) / E);
   const int R = 256 / G, TV = G * VPT;
   APF_REQUIRE(n <= INT32_MAX && (int64_t)nvec * E <= ld, APF_ERR_ARG);
-  const size_t smem = sell_ct_smem_bytes(R, TV, lmax, sizeof(TA));
+  APF_REQUIRE(halo >= 0 && R + 2 * halo <= 256, APF_ERR_ARG);
+  const size_t smem = sell_ct_smem_bytes(R, TV, lmax, sizeof(TA), halo);
   APF_REQUIRE(smem <= 200 * 1024, APF_ERR_ARG);
   // the blocks as n x (ld * sizeof(T) / 4) floats, boxes of TV vectors x R rows
   const uint64_t inner = (uint64_t)ld * sizeof(T) / 4;
-  CUtensorMap mv, my;
+  CUtensorMap mv, my, mw;
   memset(&mv, 0, sizeof(mv));
   memset(&my, 0, sizeof(my));
+  memset(&mw, 0, sizeof(mw));
+  if (halo > 0)
+    APF_REQUIRE(encode_tmap_2d(&mw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, W, inner, (uint64_t)n, ld * sizeof(T),
+                               (uint32_t)(TV * 4), (uint32_t)(R + 2 * halo), CU_TENSOR_MAP_SWIZZLE_NONE),
+                APF_ERR_CUDA);
   if (Vin)
     APF_REQUIRE(encode_tmap_2d(&mv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Vin, inner, (uint64_t)n, ld * sizeof(T),
                                (uint32_t)(TV * 4), (uint32_t)R, CU_TENSOR_MAP_SWIZZLE_NONE),
@@ -188,8 +210,8 @@ void clenshaw_sell_ct_launch(apf_ctx* ctx, int G, int VPT, int64_t n, const int6
   if (G == GG && VPT == VV) {                                                                       \
     allow_large_smem<k_clenshaw_sell_ct<T, TA, GG, VV>>(ctx->device);                              \
     k_clenshaw_sell_ct<T, TA, GG, VV><<<grid, 256, smem, ctx->stream>>>(                            \
-        n, chunk_ptr, scol, sval, lmax, W, mv, my, hv, hy, ld, nvec, coef_col, coef_scalar, alpha, \
-        Out, ctx->d_err, filter_wait_ns(ctx));                                                      \
+        n, chunk_ptr, scol, sval, lmax, W, mv, my, mw, halo, hv, hy, ld, nvec, coef_col, coef_scalar,  \
+        alpha, Out, ctx->d_err, filter_wait_ns(ctx));                                               \
     launched = true;                                                                                \
   }
   APF_SELL_CT_CASE(8, 1) APF_SELL_CT_CASE(8, 2) APF_SELL_CT_CASE(16, 1) APF_SELL_CT_CASE(8, 4)

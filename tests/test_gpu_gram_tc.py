@@ -1,7 +1,10 @@
-"""The Gram product X^H Y on the tensor cores (apf_gram_tc: FP64 columns cut
-into bf16 slices, exact FP32 accumulation of the slice products, FP64 carry)
-against the FP64 product and the definition, and whole solves that use it
-for CholQR and Rayleigh-Ritz (Alg. 4)."""
+"""The dense products of Alg. 4 on the tcgen05 tensor cores: the Gram product
+X^H Y (apf_gram_tc) and the tall block update Z = beta Z0 + alpha X M
+(apf_block_update).  Both cut FP64 values into seven 8-bit digits held in
+bf16, accumulate the digit products exactly (FP32 in TMEM per 32-row chunk,
+then 32- and 64-bit integers) and round once to FP64.  Checked against the
+FP64 product and the definition, and through whole solves that use them for
+CholQR and Rayleigh-Ritz."""
 import numpy as np
 import pytest
 

@@ -1,7 +1,8 @@
 """Every compiled variant of the FP32 Clenshaw step (Alg. 2) gives the same
 bits: SELL-8 one step per launch in each (G, VPT) shape, SELL-8 two steps per
 pass over the reverse Cuthill-McKee copy, SELL-8 in column tiles of each
-compiled tile width (also on blocks wider than 1024 columns), and CSR.  The autotuner picks among
+compiled tile width (also on blocks wider than 1024 columns), the same with
+the near rows of W staged in shared memory, and CSR.  The autotuner picks among
 them by time, so a result must not depend on the pick (a serving request gives
 the same answer alone and in a mix).  Matrices with a wide natural bandwidth
 (periodic lattices) get the permuted copy; small ones stay in natural order.
@@ -25,6 +26,7 @@ MATS = [
     ("lap2d_32", lambda: workloads.lap2d_32().matrix()),                      # natural order
     ("anderson_r_17_periodic", lambda: matrices.anderson(17, 3, 3.5, 5, False)),  # RCM copy
     ("anderson_c_70_2d", lambda: matrices.anderson(70, 2, 2.0, 6, True)),     # RCM copy
+    ("ks_like_12", lambda: matrices.ks_like_3d(12, 3, n_wells=6)),            # near rows +-4
 ]
 
 
@@ -47,7 +49,7 @@ def _variants(p, is_complex):
     out = [(3, 0, 0)]
     for kind in (1, 2):
         out += [(kind, g, v) for g, v in SELL_SHAPES if g * v >= nvec]
-    out += [(4, g, v) for g, v in CT_SHAPES]
+    out += [(kind, g, v) for kind in (4, 5) for g, v in CT_SHAPES]
     return out
 
 
@@ -91,7 +93,8 @@ def test_defect_form_agrees_across_kernels(B, ctx, name, make):
     lam = np.real(np.sum(V.conj() * AV, axis=0))
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
     outs = []
-    for kind, g, v in [(3, 0, 0), (1, 0, 0), (2, 0, 0), (2, 16, 2), (1, 32, 4), (4, 8, 2), (4, 32, 2)]:
+    for kind, g, v in [(3, 0, 0), (1, 0, 0), (2, 0, 0), (2, 16, 2), (1, 32, 4), (4, 8, 2), (4, 32, 2), (5, 8, 2),
+                       (5, 16, 4)]:
         M.set_filter_kernel(kind, g, v)
         Y = empty_like_np((A.n, p), A.is_complex)
         B.filter_apply_defect(ctx, M, coef, l1, l2, dev(V), dev(AV), dev(lam), Y)
@@ -113,7 +116,7 @@ def test_solve_is_the_same_with_every_pinned_kernel(B, ctx):
     a, b = 0.5 * (lam[i - 1] + lam[i]), 0.5 * (lam[i + c - 1] + lam[i + c])
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
     got = []
-    for kind in (0, 1, 2, 3, 4):
+    for kind in (0, 1, 2, 3, 4, 5):
         M.set_filter_kernel(kind)
         r = B.solve(ctx, M, B.default_params(a=a, b=b, p=24, seed=3, filter_precision=B.APF_FILTER_F32_DEFECT))
         got.append(r.eigvals())
@@ -127,7 +130,7 @@ def test_solve_is_the_same_with_every_pinned_kernel(B, ctx):
 def test_set_filter_kernel_rejects_bad_kind(B, ctx):
     A = matrices.anderson(5, 3, 4.0, 3, False)
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
-    for kind in (-1, 5):
+    for kind in (-1, 6):
         with pytest.raises(B.ApfError) as ei:
             M.set_filter_kernel(kind)
         assert ei.value.status == B.APF_ERR_ARG
@@ -149,7 +152,7 @@ def test_column_tiles_on_wide_blocks(B, ctx, is_complex):
     ref = clenshaw_apply(As, coef, l1, l2, X)
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
     outs = []
-    for kind, g, v in [(3, 0, 0)] + [(4, g, v) for g, v in CT_SHAPES]:
+    for kind, g, v in [(3, 0, 0)] + [(k, g, v) for k in (4, 5) for g, v in CT_SHAPES]:
         M.set_filter_kernel(kind, g, v)
         Y = empty_like_np((A.n, p), is_complex)
         B.filter_apply(ctx, M, coef, l1, l2, dev(X), Y, B.APF_FILTER_F32)

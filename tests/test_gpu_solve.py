@@ -100,6 +100,12 @@ def test_complex_anderson_small(B, ctx, prec):
     out = _solve(B, ctx, A, a, b, 20, 7, filter_precision=_prec(B, prec))
     _check(out, A, lam[(lam >= a) & (lam <= b)])
     assert dense.interval_count(A.to_dense(), a, b) == out["lam"].size
+    # the statistics name the FP32 step kernel that ran (none for the FP64 filter)
+    st = out["stats"]
+    if prec == "F64":
+        assert st["filter_kind"] == -1
+    else:
+        assert st["filter_kind"] in (1, 2, 3, 4) and st["filter_g"] in (4, 8, 16, 32) and st["filter_vpt"] >= 1
 
 
 @pytest.mark.parametrize("prec", PREC)

@@ -5,9 +5,10 @@ against exact rational arithmetic:
  - a value x with |x| < 2^E becomes F = round(x 2^(55 - E)), cut into seven
    balanced base-256 digits in [-128, 128] (held exactly by bf16) that rebuild
    F exactly, so x is represented to within 2^(E - 56);
- - a 32-row chunk's digit-product sums on a diagonal stay below 2^22 (FP32
-   adds them exactly in any order, and the hi / lo carry of the kernel is
-   exact integer arithmetic);
+ - a 32-row chunk's digit-product sums on diagonal d stay within
+   (d + 1) 2^19, so the kernel's drain period of floor(32 / (d + 1)) chunks
+   keeps every FP32 partial sum an integer within 2^24 (exact in any order),
+   and the hi / lo carry of the kernel is exact integer arithmetic;
  - the carried sums give the product to within n 2^(E_a + E_b - 55);
  - the digits the model computes equal a direct integer computation from the
    bits of x (the kernel's method) on random, tiny, huge and signed values.
@@ -106,6 +107,27 @@ def test_chunk_sums_fit_fp32_and_the_carry():
     assert hi * 2 ** 16 < 2 ** 63 and lo * 2 ** 16 < 2 ** 63
 
 
+def test_drain_periods_keep_fp32_sums_exact():
+    """Diagonal d has d + 1 digit pairs: a 32-row chunk adds at most
+    (d + 1) x 32 x 128 x 128 = (d + 1) 2^19 to its sum.  The kernel reads the
+    FP32 accumulator of d out every floor(32 / (d + 1)) chunks, the longest
+    period whose worst case stays within 2^24 (the integers FP32 holds
+    exactly); hi and lo then gain less than 2^36 and 2^46 per chunk, so 2^16
+    chunks stay inside 64 bits."""
+    shift = [16, 8, 0, 24, 16, 8, 0]
+    hi = lo = 0
+    for d in range(S):
+        per = 32 // (d + 1)
+        worst = (d + 1) * KC * 128 * 128
+        assert per * worst <= 2 ** 24 < (per + 1) * worst
+        if d < 3:
+            hi += worst << shift[d]
+        else:
+            lo += worst << shift[d]
+    assert hi < 2 ** 36 and lo < 2 ** 46
+    assert hi * 2 ** 16 < 2 ** 63 and lo * 2 ** 16 < 2 ** 63
+
+
 def test_carried_product_error_bound():
     n, pa, pb = 300, 3, 4
     X = rng.uniform_block(5, rng.STREAM_TEST, n, pa, False) * np.array([1e-3, 1.0, 40.0])
@@ -116,15 +138,23 @@ def test_carried_product_error_bound():
     DY = [[_digits(Y[i, b], ey[b]) for i in range(n)] for b in range(pb)]
     for a in range(pa):
         for b in range(pb):
+            # the kernel's schedule: per-diagonal sums over drain periods of
+            # floor(32 / (d + 1)) chunks, carried into hi / lo at each period's end
             hi = lo = 0
-            for c0 in range(0, n, KC):
-                P = [0] * S
+            acc = [0] * S
+            nch = (n + KC - 1) // KC
+            for c in range(nch):
+                c0 = c * KC
                 for d in range(S):
                     for s in range(d + 1):
-                        P[d] += sum(DX[a][i][s] * DY[b][i][d - s] for i in range(c0, min(n, c0 + KC)))
-                    assert abs(P[d]) < 2 ** 22
-                hi += (P[0] << 16) + (P[1] << 8) + P[2]
-                lo += (P[3] << 24) + (P[4] << 16) + (P[5] << 8) + P[6]
+                        acc[d] += sum(DX[a][i][s] * DY[b][i][d - s] for i in range(c0, min(n, c0 + KC)))
+                    assert abs(acc[d]) <= 2 ** 24
+                    if (c + 1) % (32 // (d + 1)) == 0 or c == nch - 1:
+                        if d < 3:
+                            hi += acc[d] << (16, 8, 0)[d]
+                        else:
+                            lo += acc[d] << (24, 16, 8, 0)[d - 3]
+                        acc[d] = 0
             got = Fraction(hi * 2 ** 32 + lo) * Fraction(2) ** (ex[a] + ey[b] - 62)
             exact = sum(Fraction(float(X[i, a])) * Fraction(float(Y[i, b])) for i in range(n))
             bound = n * Fraction(2) ** (ex[a] + ey[b] - 55)
