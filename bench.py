@@ -79,9 +79,10 @@ def parse():
                     help="time N tensor-core Gram products X^H X and N block updates X M on the workload's "
                          "n x p block instead of solves")
     ap.add_argument("--shape", default="0,0",
-                    help="filter-only mode: step kernel shape 'G,VPT' (lanes per row, vectors per lane; 0,0 = default)")
+                    help="with --kernel: step kernel shape 'G,VPT' (lanes per row, vectors per lane; 0,0 = default)")
     ap.add_argument("--kernel", type=int, default=0,
-                    help="filter-only: pin the step kernel (0 autotune, 1 SELL, 2 SELL two-step, 3 CSR)")
+                    help="pin the FP32 step kernel (0 autotune, 1 SELL, 2 SELL two-step, 3 CSR, 4 SELL column "
+                         "tiles, 5 column tiles with near rows staged)")
     ap.add_argument("--requests", type=int, default=24, help="serving workload: number of requests")
     ap.add_argument("--compare-single", action="store_true",
                     help="slice workloads: also solve the slices one after another")
@@ -274,6 +275,8 @@ def ours_arm(args, dist):
     A = w.matrix()
     ctx = B.Context(dist.local, stream=stream.cuda_stream)
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
+    if args.kernel and not args.filter_only:  # a pinned step kernel instead of the autotuner's pick
+        M.set_filter_kernel(args.kernel, *(int(t) for t in args.shape.split(",")))
     prec = {"f64": B.APF_FILTER_F64, "f32": B.APF_FILTER_F32, "f32_defect": B.APF_FILTER_F32_DEFECT}[args.precision]
     p_used = w.p if args.p < 0 else args.p
     prm = B.default_params(a=w.a, b=w.b, p=p_used, seed=w.seed + 1000 * dist.rank, filter_precision=prec,

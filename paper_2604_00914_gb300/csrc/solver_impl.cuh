@@ -200,9 +200,9 @@ static void pinned_shape(Stepper<S>& st, int nvec) {
 }
 
 // Autotuner: time each candidate shape on the live buffers (one warm-up pass
-// and four timed steps each; W, Y and an in-place V = output distinct, as in
-// the recurrence) and keep the fastest per (element size, ld, width) in the
-// matrix.  All shapes do the same arithmetic in the same order, so the choice
+// and four timed steps each, used as the recurrence uses them: Y fixed, the
+// output written over V, and each step's output the next step's W) and keep
+// the fastest per (element size, ld, width) in the matrix.  All shapes do the same arithmetic in the same order, so the choice
 // changes the time, never the result.
 template <class S>
 static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Yb, S* Ob) {
@@ -300,7 +300,9 @@ static void tune_stepper(Stepper<S>& st, int64_t p, const S* Wb, const S* Yb, S*
         t.pair(const_cast<S*>(Wb), Ob, Ob, Yb, p, nullptr, (Real)0.5, nullptr, (Real)0.25);
         t.pair(const_cast<S*>(Wb), Ob, Ob, Yb, p, nullptr, (Real)0.5, nullptr, (Real)0.25);
       } else {
-        for (int r = 0; r < 4; ++r) t(Wb, Ob, Yb, p, nullptr, (Real)0.5, (Real)2, Ob);
+        // each step reads what the one before wrote, as in the recurrence
+        S* b[2] = {const_cast<S*>(Wb), Ob};
+        for (int r = 0; r < 4; ++r) t(b[r & 1], b[(r + 1) & 1], Yb, p, nullptr, (Real)0.5, (Real)2, b[(r + 1) & 1]);
       }
     };
     if (&c == &cands[0]) run();  // the GPU's clocks settle before the first timing

@@ -166,7 +166,7 @@ def anderson3d_r_80_slices() -> SliceWorkload:
     seeded uneven target counts in [20, 150] (56..141 here, 1,480 in all),
     starting above the 200th eigenvalue, edges from the oracle's count
     estimate (stored in tests/golden); block m = ceil(1.5 count) per slice
-    (2,232 columns in all)."""
+    (2,224 columns in all)."""
     import math
     path = os.path.join(_GOLDEN, "slices_anderson3d_r_80.json")
     with open(path) as f:
