@@ -127,6 +127,7 @@ typedef struct {
                                 apf_matrix_set_filter_kernel, CSR reported as 3); -1 for the FP64 filter
                                 and for a served request whose steps all ran in the batched launch */
   int32_t filter_g, filter_vpt;  /* its shape: lanes per row, 16-byte vectors per lane */
+  int64_t filter_graph_replays;  /* filter applications replayed from a captured CUDA graph */
 } apf_stats;
 
 #define APF_MAX_P 1024

@@ -72,6 +72,7 @@ class apf_stats(C.Structure):
         ("filter_steps", C.c_int64), ("filter_step_bytes", C.c_double),
         ("trace_estimate", C.c_double), ("p_used", C.c_int64),
         ("filter_kind", C.c_int32), ("filter_g", C.c_int32), ("filter_vpt", C.c_int32),
+        ("filter_graph_replays", C.c_int64),
     ]
 
     def as_dict(self):

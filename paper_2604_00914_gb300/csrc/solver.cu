@@ -259,6 +259,7 @@ static void solve_slices_t(apf_ctx* ctx, const apf_matrix* A, int ns, const doub
   DBuf wc(sizeof(double) * (size_t)(ldc + 8), ctx->stream, true);
   FilterState<T> fs;
   fs.init(ctx, A, ldc, bd.l1, bd.l2, std::vector<double>(), prm->filter_precision);
+  fs.graphs_on = prm->filter_graphs != 0;  // recurring applications of all slices replay as one graph
   APF_CUDA(cudaStreamSynchronize(ctx->stream));
   st.ms_setup = std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
 

@@ -31,6 +31,7 @@ struct FilterCount {
   double bytes = 0.0;     // algorithmic bytes of the launched kernels
   double step_bytes = 0.0;  // algorithmic bytes of the same steps run one per launch
   int kind = -1, G = 0, VPT = 0;  // FP32 step kernel of the first (widest) application
+  int64_t graph_replays = 0;      // applications replayed from a captured CUDA graph
   template <class S>
   void note(const Stepper<S>& st) {
     if (kind < 0) { kind = st.kind == 0 ? 3 : st.kind; G = st.G; VPT = st.VPT; }  // internal 0 = CSR
@@ -548,6 +549,7 @@ struct FilterState {
   struct GraphEntry {
     int form = 0, k = 0, kind = 0, G = 0, VPT = 0, seen = 0;
     int64_t p = 0;
+    uint64_t sig = 0;  // batched filters: per-column degrees and coefficient table
     const void* in = nullptr;
     cudaGraphExec_t exec = nullptr;
     void* out = nullptr;
@@ -556,6 +558,7 @@ struct FilterState {
   };
   std::vector<GraphEntry> graphs;
   bool graphs_on = false;
+  DBuf Fcols;  // coefficient table of a batched filter ((K + 1) x ld), kept so graphs can replay on it
   std::vector<double> a;         // host a_j
   int precision = APF_FILTER_F64;
   int kmax = 0;
@@ -611,16 +614,16 @@ struct FilterState {
   // buffer) directly or through a cached graph.
   template <class S, class Body>
   S* run_recurrence(int form, int k, int64_t p, const void* in, const Stepper<S>& st, cudaEvent_t ev0,
-                    cudaEvent_t ev1, FilterCount* fc, Body&& body) {
+                    cudaEvent_t ev1, FilterCount* fc, Body&& body, uint64_t sig = 0) {
     if (!graphs_on || st.pairs()) return body(ev0, ev1, fc);
     GraphEntry* g = nullptr;
     for (auto& e : graphs)
       if (e.form == form && e.k == k && e.p == p && e.in == in && e.kind == st.kind && e.G == st.G &&
-          e.VPT == st.VPT)
+          e.VPT == st.VPT && e.sig == sig)
         g = &e;
     if (g == nullptr) {
       GraphEntry e;
-      e.form = form; e.k = k; e.p = p; e.in = in; e.kind = st.kind; e.G = st.G; e.VPT = st.VPT;
+      e.form = form; e.k = k; e.p = p; e.in = in; e.kind = st.kind; e.G = st.G; e.VPT = st.VPT; e.sig = sig;
       graphs.push_back(e);
       g = &graphs.back();
     }
@@ -657,6 +660,7 @@ struct FilterState {
     APF_CUDA(cudaGraphLaunch(g->exec, ctx->stream));
     if (ev1) APF_CUDA(cudaEventRecord(ev1, ctx->stream));
     ctx->launches += g->launches;
+    fc->graph_replays += 1;
     fc->launches += g->fc.launches;
     fc->steps += g->fc.steps;
     fc->bytes += g->fc.bytes;
@@ -760,14 +764,30 @@ struct FilterState {
     DBuf kcd((size_t)p * sizeof(int32_t), ctx->stream, false), cod((size_t)p * sizeof(int64_t), ctx->stream, false);
     APF_CUDA(cudaMemcpyAsync(kcd.p, kc.data(), (size_t)p * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
     APF_CUDA(cudaMemcpyAsync(cod.p, coff.data(), (size_t)p * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+    // the coefficient table stays in one buffer (grown when needed) and the
+    // recurrence's launches depend only on the per-column degrees and that
+    // buffer, so a recurring application replays as a CUDA graph
+    const size_t fbytes = (size_t)(K + 1) * ld * (precision == APF_FILTER_F64 ? sizeof(double) : sizeof(float));
+    if (Fcols.bytes < fbytes) Fcols.alloc(fbytes + fbytes / 4, ctx->stream, false);
+    uint64_t sig = 1469598103934665603ull;  // FNV-1a over the degrees and the table's address
+    auto mix = [&](uint64_t v) {
+      for (int b = 0; b < 8; ++b) { sig ^= (v >> (8 * b)) & 0xFF; sig *= 1099511628211ull; }
+    };
+    for (int32_t kk : kc) mix((uint64_t)(uint32_t)kk);
+    mix((uint64_t)(uintptr_t)Fcols.p);
     if (precision == APF_FILTER_F64) {
       APF_CUDA(cudaMemsetAsync(B1.p, 0, B1.bytes, ctx->stream));
       APF_CUDA(cudaMemsetAsync(B2.p, 0, B2.bytes, ctx->stream));
-      DBuf Fd((size_t)(K + 1) * ld * sizeof(double), ctx->stream, false);
       coef_columns<double>(ctx, p, ld, K, coef_dev, cod.as<int64_t>(), kcd.as<int32_t>(), nullptr, l1, l2,
-                           Fd.as<double>(), nullptr);
-      T* out = clenshaw_plain_cols<T>(ctx, stepper64(), n, nnz, V, ld, Fd.as<double>(), K, act_plain, B1.as<T>(),
-                                      B2.as<T>(), ev0, ev1, fc);
+                           Fcols.as<double>(), nullptr);
+      const Stepper<T> s64 = stepper64();
+      T* out = run_recurrence<T>(
+          3, K, p, V, s64, ev0, ev1, fc,
+          [&](cudaEvent_t e0, cudaEvent_t e1, FilterCount* f) {
+            return clenshaw_plain_cols<T>(ctx, s64, n, nnz, V, ld, Fcols.as<double>(), K, act_plain, B1.as<T>(),
+                                          B2.as<T>(), e0, e1, f);
+          },
+          sig);
       copy_block<T>(ctx, n, p, out, ld, X, ld);
       return;
     }
@@ -775,22 +795,32 @@ struct FilterState {
     if (fc) fc->note(st);
     APF_CUDA(cudaMemsetAsync(B1.p, 0, B1.bytes, ctx->stream));
     APF_CUDA(cudaMemsetAsync(B2.p, 0, B2.bytes, ctx->stream));
-    DBuf Ff((size_t)(K + 1) * ld * sizeof(float), ctx->stream, false);
+    float* Ff = Fcols.as<float>();
     if (precision == APF_FILTER_F32_DEFECT && AV != nullptr && lam != nullptr) {
       DBuf scratch((size_t)p * sizeof(double), ctx->stream, false);
       residual_norms<T>(ctx, n, p, AV, V, ld, lam, scratch.as<double>(), Y32.as<TL>(), l1, rows_out(st));
-      coef_columns<float>(ctx, p, ld, K, coef_dev, cod.as<int64_t>(), kcd.as<int32_t>(), lam, l1, l2,
-                          Ff.as<float>(), rho.as<double>());
-      TL* D = clenshaw_defect_cols<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, Ff.as<float>(), K, act_def,
-                                       B1.as<TL>(), B2.as<TL>(), ev0, ev1, fc);
+      coef_columns<float>(ctx, p, ld, K, coef_dev, cod.as<int64_t>(), kcd.as<int32_t>(), lam, l1, l2, Ff,
+                          rho.as<double>());
+      TL* D = run_recurrence<TL>(
+          4, K, p, Y32.p, st, ev0, ev1, fc,
+          [&](cudaEvent_t e0, cudaEvent_t e1, FilterCount* f) {
+            return clenshaw_defect_cols<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, Ff, K, act_def, B1.as<TL>(),
+                                            B2.as<TL>(), e0, e1, f);
+          },
+          sig);
       defect_combine<T>(ctx, n, p, V, ld, rho.as<double>(), D, ld, X, ld, rows_out(st));
       return;
     }
     cast_block_rows<T, TL>(ctx, n, p, V, ld, Y32.as<TL>(), ld, rows_in(st));
-    coef_columns<float>(ctx, p, ld, K, coef_dev, cod.as<int64_t>(), kcd.as<int32_t>(), nullptr, l1, l2,
-                        Ff.as<float>(), nullptr);
-    TL* out = clenshaw_plain_cols<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, Ff.as<float>(), K, act_plain,
-                                      B1.as<TL>(), B2.as<TL>(), ev0, ev1, fc);
+    coef_columns<float>(ctx, p, ld, K, coef_dev, cod.as<int64_t>(), kcd.as<int32_t>(), nullptr, l1, l2, Ff,
+                        nullptr);
+    TL* out = run_recurrence<TL>(
+        5, K, p, Y32.p, st, ev0, ev1, fc,
+        [&](cudaEvent_t e0, cudaEvent_t e1, FilterCount* f) {
+          return clenshaw_plain_cols<TL>(ctx, st, n, nnz, Y32.as<TL>(), ld, Ff, K, act_plain, B1.as<TL>(),
+                                         B2.as<TL>(), e0, e1, f);
+        },
+        sig);
     cast_block_rows<TL, T>(ctx, n, p, out, ld, X, ld, rows_out(st));
   }
 };
@@ -1215,6 +1245,7 @@ static void finish_stats(apf_ctx* ctx, const std::vector<IterEv>& iev, const Fil
   st->filter_kind = fc.kind;
   st->filter_g = fc.G;
   st->filter_vpt = fc.VPT;
+  st->filter_graph_replays = fc.graph_replays;
 }
 
 struct Bounds {

@@ -38,8 +38,10 @@ def _slices(lam, specs):
     return np.array(a), np.array(b)
 
 
-def _run_slices(B, ctx, A, a, b, p, seed, **kw):
+def _run_slices(B, ctx, A, a, b, p, seed, kernel=0, **kw):
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
+    if kernel:
+        M.set_filter_kernel(kernel)
     prm = B.default_params(seed=seed, **kw)
     r = B.solve_slices(ctx, M, a, b, p, prm, allow_no_convergence=True)
     out = dict(status=r.status, lam=r.eigvals(), V=r.eigvecs(A.n, A.is_complex), res=r.residuals(),
@@ -125,6 +127,29 @@ def test_wide_slices_beyond_1024_columns(B, ctx):
     assert np.max(np.abs(out["lam"] - lam[inside])) <= 1e-10 * np.abs(lam).max()
     res = np.linalg.norm(A.to_scipy() @ out["V"] - out["V"] * out["lam"], axis=0)
     assert res.max() <= 1e-10 * np.abs(lam).max()
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_slice_graph_replay_gives_the_same_solve(B, ctx, prec):
+    """Recurring batched filter applications (the same per-column degrees and
+    widths: a fixed degree, before the first lock) replay as one CUDA graph
+    for all slices: the same eigenvalues, residuals, counts and launch
+    counters as plain launches.  The FP32 step is pinned to one step per
+    launch: the two-step kernel's pass counters rule out graphs."""
+    A = matrices.anderson(10, 3, 5.0, 21, False)
+    lam = np.linalg.eigvalsh(A.to_dense())
+    a, b = _slices(lam, [(520, 9), (300, 5), (90, 12)])
+    p = np.array([16, 12, 20])
+    kw = dict(filter_precision=getattr(B, "APF_FILTER_" + prec), k_fixed=300, kernel=1)
+    on = _run_slices(B, ctx, A, a, b, p, 5, filter_graphs=1, **kw)
+    off = _run_slices(B, ctx, A, a, b, p, 5, filter_graphs=0, **kw)
+    assert on["status"] == off["status"] == 0
+    assert np.array_equal(on["lam"], off["lam"]) and np.array_equal(on["res"], off["res"])
+    assert list(on["counts"]) == list(off["counts"])
+    for key in ("iterations", "filter_launches", "filter_steps", "spmv_columns", "gpu_launches"):
+        assert on["stats"][key] == off["stats"][key], key
+    assert on["stats"]["filter_graph_replays"] > 0 and off["stats"]["filter_graph_replays"] == 0
+    _check_against_definition(on, A, lam, a, b)
 
 
 @pytest.mark.parametrize("prec", PREC)

@@ -35,8 +35,10 @@ def _prec(B, name):
     return getattr(B, "APF_FILTER_" + name)
 
 
-def _solve(B, ctx, A, a, b, p, seed, **kw):
+def _solve(B, ctx, A, a, b, p, seed, kernel=0, **kw):
     M = B.Matrix.from_csr(ctx, A.n, A.rowptr, A.colidx, A.vals)
+    if kernel:
+        M.set_filter_kernel(kernel)
     prm = B.default_params(a=a, b=b, p=p, seed=seed, **kw)
     r = B.solve(ctx, M, prm, allow_no_convergence=True)
     out = dict(status=r.status, lam=r.eigvals(), V=r.eigvecs(A.n, A.is_complex), res=r.residuals(),
@@ -236,5 +238,23 @@ def test_graph_replay_gives_the_same_solve(B, ctx, prec):
     assert np.array_equal(on["lam"], off["lam"]) and np.array_equal(on["res"], off["res"])
     for key in ("iterations", "filter_launches", "filter_steps", "spmv_columns", "gpu_launches"):
         assert on["stats"][key] == off["stats"][key], key
+    assert off["stats"]["filter_graph_replays"] == 0
     if prec != "F32":
         assert on["status"] == 0
+
+
+@pytest.mark.parametrize("prec", ["F64", "F32_DEFECT"])
+def test_graph_replay_runs_at_a_fixed_degree(B, ctx, prec):
+    """At a fixed degree every outer iteration before the first lock repeats
+    the same filter application, so from the third one on it replays as a
+    graph; the result equals the plain launches'.  The FP32 step is pinned
+    to one step per launch (the two-step kernel is never captured)."""
+    A = matrices.anderson(9, 3, 4.0, 14, True)
+    lam = np.linalg.eigvalsh(A.to_dense())
+    a, b = _interval_around(lam, 0.4, 8)
+    kw = dict(filter_precision=_prec(B, prec), k_fixed=300, kernel=1)
+    on = _solve(B, ctx, A, a, b, 16, 5, filter_graphs=1, **kw)
+    off = _solve(B, ctx, A, a, b, 16, 5, filter_graphs=0, **kw)
+    assert on["status"] == off["status"] == 0
+    assert np.array_equal(on["lam"], off["lam"]) and np.array_equal(on["res"], off["res"])
+    assert on["stats"]["filter_graph_replays"] > 0 and off["stats"]["filter_graph_replays"] == 0
