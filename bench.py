@@ -761,7 +761,8 @@ def filter_only(args, dist, B, ctx, M, A, w, peak, peak_kind):
 def dense_only(args, dist, B, ctx, A, w, stream):
     """Time the dense products of one outer iteration on the tensor cores:
     G = X^H X (apf_gram_tc) and Z = X M (apf_block_update) on the workload's
-    n x p block, with CUDA events on the library's stream.  The tensor-pipe
+    n x p block, and the p x p eigensolve of Rayleigh-Ritz (apf_eigh_small),
+    with CUDA events on the library's stream.  The tensor-pipe
     rate counts the bf16 MMAs the digit scheme issues: 28 digit pairs x
     2 x 128 x 32 x 32 flops per 32-row chunk of each 128 x 32 output tile."""
     import math
@@ -789,6 +790,21 @@ def dense_only(args, dist, B, ctx, A, w, stream):
     torch.cuda.synchronize()
     gram_ms = ev[0].elapsed_time(ev[1]) / args.dense_only
     upd_ms = ev[1].elapsed_time(ev[2]) / args.dense_only
+    # the p x p Hermitian eigensolve of Rayleigh-Ritz (one-sided Jacobi) on a
+    # Gram-like matrix of the same size
+    Hm = torch.from_numpy(rng.uniform_block(w.seed, rng.STREAM_TEST, p, p, cplx)).cuda()
+    Hm = (Hm + Hm.conj().T).contiguous()
+    wv = torch.empty(p, dtype=torch.float64, device="cuda")
+    Um = torch.empty_like(Hm)
+    torch.cuda.synchronize()  # Hm is written on torch's stream, read on the library's
+    B.eigh_small(ctx, Hm, wv, Um)
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    for _ in range(args.dense_only):
+        B.eigh_small(ctx, Hm, wv, Um)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    eigh_ms = ev[2].elapsed_time(ev[3]) / args.dense_only
     chunk_flops = 28 * 2 * 128 * 32 * 32  # 28 pairs x (2 flops x M 128 x N 32 x K 32)
     pP, nP = 128 * math.ceil(p / 128), 32 * math.ceil(p / 32)
     gram_tiles = (pP // 128) * (C * nP // 32)
@@ -810,6 +826,7 @@ def dense_only(args, dist, B, ctx, A, w, stream):
             "update_ms": upd_ms, "update_tensor_tflops": upd_mma / upd_ms / 1e9,
             "update_tensor_frac_of_bf16_peak": upd_mma / upd_ms / 1e9 / bf16,
             "update_fp64_equivalent_tflops": fp64_flops / upd_ms / 1e9,
+            "eigh_small_ms": eigh_ms,
             "bf16_peak_tflops": bf16, "calls": args.dense_only}), flush=True)
 
 
