@@ -251,8 +251,11 @@ def reference_arm(args, dist):
         if i >= args.warmup:
             vals.append(cpu_eigenpairs_per_s(sample, prof))
     v = statistics.median(vals)
+    # a step is one whole solve of the workload, at the sampled rate
+    ms_solve = 1e3 * prof["eigenpairs"] / v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": sample["cores"], "kind": "oracle",
