@@ -136,8 +136,12 @@ typedef struct {
 
 /* ---- context --------------------------------------------------------- */
 
-/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
- * to order all work on, or NULL for a stream owned by the context. */
+/* Create a context on CUDA device `device`: the state that the paper's
+ * solver keeps across the outer iterations of Alg. 4 (device buffers, the
+ * stream, device error word, workspace) lives here.  `cuda_stream` is a
+ * cudaStream_t to order all work on (not owned), or NULL for a stream owned
+ * by the context.  *out is released by apf_destroy.  APF_ERR_ARG for a bad
+ * device or null out; APF_ERR_CUDA when the device cannot be used. */
 apf_status apf_create(apf_ctx** out, int device, void* cuda_stream);
 /* Destroy a context.  Destroy its matrices and results first: they refer to it. */
 apf_status apf_destroy(apf_ctx* ctx);
@@ -240,8 +244,12 @@ apf_status apf_solve_slices(apf_ctx* ctx, const apf_matrix* A, int32_t nslices, 
  * the number the result was solved with (APF_ERR_ARG otherwise, also for a
  * result of apf_solve). */
 apf_status apf_result_slice_counts(const apf_result* r, int32_t nslices, int64_t* counts);
+/* The result of Alg. 4: the locked set L of eigenpairs inside [a, b] at
+ * exit.  The accessors below read it; none transfers ownership, and every one
+ * returns APF_ERR_ARG for a null argument.  e = |L|, the count of eigenvalues
+ * in [a, b] (Alg. 4 output). */
 apf_status apf_result_count(const apf_result* r, int64_t* e);
-/* e eigenvalues, ascending, to host memory. */
+/* e eigenvalues, ascending, to host memory (host_out: e doubles, caller-owned). */
 apf_status apf_result_eigvals(const apf_result* r, double* host_out);
 /* n x e eigenvectors, column-major with leading dimension ld >= n (column j
  * belongs to eigenvalue j), of the matrix dtype; `out_on_device` selects
@@ -251,11 +259,13 @@ apf_status apf_result_eigvecs(const apf_result* r, void* out, int64_t ld, int32_
  * never exceeds the spectral radius, so these bound the residuals relative to
  * the true ||A|| from above). */
 apf_status apf_result_residuals(const apf_result* r, double* host_out);
+/* The counters of Table 2 (iterations, SpMV columns, degrees) and stage times. */
 apf_status apf_result_stats(const apf_result* r, apf_stats* out);
 /* Per-iteration history, up to `cap` records of 6 doubles each:
  * (degree, active width, e, locked this iteration, n_lock before, max in-interval residual / ||A||).
  * Returns the number of records in *count. */
 apf_status apf_result_history(const apf_result* r, double* host_out, int32_t cap, int32_t* count);
+/* Free a result (and, for a served request, the request's own context). */
 apf_status apf_result_destroy(apf_result* r);
 
 /* ---- serving: many solves on one GPU -------------------------------------- */
