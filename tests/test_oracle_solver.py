@@ -228,3 +228,53 @@ def test_shifted_cholqr_branch_runs_with_the_published_shift(monkeypatch):
     D = R.conj().T @ R - X.conj().T @ X
     assert np.max(np.abs(D - s * np.eye(p))) <= 0.05 * s
     assert np.allclose(np.real(np.diag(D)), s, rtol=0.05)
+
+
+@pytest.mark.parametrize("is_complex", [False, True])
+def test_project_out_is_the_orthogonal_projector(is_complex):
+    """X - V (V^H X) twice: the result is orthogonal to the locked V, what was
+    removed lies in span(V), projecting again changes nothing, and a block
+    already orthogonal to V comes back unchanged (to rounding)."""
+    n, m, p = 200, 7, 5
+    V, _ = np.linalg.qr(rng.uniform_block(21, rng.STREAM_TEST, n, m, is_complex))
+    X = rng.uniform_block(22, rng.STREAM_TEST, n, p, is_complex)
+    Y = fsi.project_out(V, X)
+    assert np.max(np.abs(V.conj().T @ Y)) < 1e-14 * np.abs(X).max() * n
+    D = X - Y                                   # the removed part
+    assert np.max(np.abs(D - V @ (V.conj().T @ D))) < 1e-13 * np.abs(X).max()
+    assert np.max(np.abs(fsi.project_out(V, Y) - Y)) < 1e-14 * np.abs(X).max() * n
+    Z = Y / np.abs(Y).max()
+    assert np.max(np.abs(fsi.project_out(V, Z) - Z)) < 1e-13
+    assert fsi.project_out(V[:, :0], X) is X   # nothing locked: nothing to remove
+
+
+@pytest.mark.parametrize("is_complex", [False, True])
+def test_rayleigh_ritz_on_an_invariant_subspace(is_complex):
+    """Alg. 1 on a basis Q of an invariant subspace (any orthonormal mixing of
+    eigenvectors of A) returns exactly those eigenvalues, with Ritz vectors
+    that are eigenvectors; on a generic subspace the Ritz values lie inside the
+    spectrum and the Ritz vectors are orthonormal."""
+    As, Ad = _small_hermitian(90, 8, is_complex)
+    lam, U = np.linalg.eigh(Ad)
+    idx = [3, 17, 40, 41, 77]
+    W, _ = np.linalg.qr(rng.uniform_block(23, rng.STREAM_TEST, len(idx), len(idx), is_complex))
+    Q = U[:, idx] @ W                           # same span, mixed basis
+    th, V = fsi.rayleigh_ritz(As, Q)
+    assert np.max(np.abs(th - lam[idx])) < 1e-12 * np.abs(lam).max()
+    assert np.max(fsi.residual_norms(As, V, th)) < 1e-12 * np.abs(lam).max()
+    Qg, _ = np.linalg.qr(rng.uniform_block(24, rng.STREAM_TEST, 90, 6, is_complex))
+    th, V = fsi.rayleigh_ritz(As, Qg)
+    assert np.all(th >= lam[0] - 1e-12) and np.all(th <= lam[-1] + 1e-12)
+    assert np.max(np.abs(V.conj().T @ V - np.eye(6))) < 1e-13
+
+
+def test_residual_norms_of_exact_and_shifted_pairs():
+    """||A v - mu v|| is zero (to rounding) for an eigenpair and equals
+    |lambda - mu| for an eigenvector of unit norm paired with a wrong value."""
+    As, Ad = _small_hermitian(60, 9, True)
+    lam, U = np.linalg.eigh(Ad)
+    r = fsi.residual_norms(As, U[:, :4], lam[:4])
+    assert np.max(r) < 1e-13 * np.abs(lam).max()
+    shift = np.array([0.5, -0.25, 1e-3, 2.0])
+    r = fsi.residual_norms(As, U[:, :4], lam[:4] + shift)
+    assert np.allclose(r, np.abs(shift), rtol=1e-10, atol=1e-13)
