@@ -651,10 +651,13 @@ def slices_arm(args, dist):
         "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "f32_defect": "f32+f64"}[args.precision],
         "data": "synthetic", "mode": "slices",
         "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "slices": len(w.a),
-                   "intervals": [[x, y] for x, y in zip(w.a, w.b)], "p": "estimated (Sec. 3.4)",
+                   "intervals": [[x, y] for x, y in zip(w.a, w.b)],
+                   "p": "estimated (Sec. 3.4)" if not any(w.p) else [int(q) for q in w.p],
                    "p_total": st["p_used"], "count_estimate": st["trace_estimate"],
                    "slice_counts": [int(c) for c in counts], "status": statuses,
                    "iterations": st["iterations"], "max_residual": st["max_residual"],
+                   "graph_replays": st["filter_graph_replays"],
+                   "step_kernel": {"kind": st["filter_kind"], "G": st["filter_g"], "VPT": st["filter_vpt"]},
                    "precision": args.precision, "parallelism": f"replicas{args.gpus}"},
         "roofline": {"kernel": "Clenshaw filter step (FP32 real, all slices per launch)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
